@@ -1,0 +1,67 @@
+"""Overlapping subdomains and their extensions (Sec. 3; Sec. 6 step 1; Sec. 7.1).
+
+Given node owner labels (the graph partition of Sec. 6 step 1):
+  P_i        nodes owned by subdomain i;
+  omega_i    elements with at least one node in P_i (Fig. 1 caption: "elements that
+             have at least one node belonging to a specific subgraph"); two subdomains
+             then overlap in one layer of elements;
+  ball       nodes within r mesh-edge hops of P_i (the r-hops of Sec. 7.1);
+  T_i^+      elements touching the ball (so every ball node is interior to omega_i^+);
+  I          free nodes of T_i^+ whose incident elements all lie in T_i^+ (interior
+             of omega_i^+, Sec. 4), B = the other free nodes of T_i^+ (on
+             d omega_i^+ minus d Omega);
+  omega DOFs free nodes of omega_i (the space V_i);
+  owned      free nodes of P_i: the nodes kept by the stitching restriction D_i.
+Hops run over the edges of the tetrahedra (every pair of vertices of an element).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def node_adjacency(tets, n_nodes):
+    r = np.repeat(tets, 4, axis=1).ravel()
+    c = np.tile(tets, (1, 4)).ravel()
+    A = sp.coo_matrix((np.ones(len(r), dtype=np.int8), (r, c)), shape=(n_nodes, n_nodes))
+    return A.tocsr()
+
+
+def subdomain_sets(mesh, owner, i, r_hops, adj=None):
+    n = mesh.n_nodes
+    tets = mesh.tets
+    if adj is None:
+        adj = node_adjacency(tets, n)
+    P = owner == i
+    ball = P.copy()
+    for _ in range(r_hops):
+        ball = ball | ((adj @ ball.astype(np.int8)) > 0)
+    plus_t = np.flatnonzero(ball[tets].any(axis=1))
+    omega_t = np.flatnonzero(P[tets].any(axis=1))
+    cnt_all = np.bincount(tets.ravel(), minlength=n)
+    cnt_plus = np.bincount(tets[plus_t].ravel(), minlength=n)
+    in_plus = cnt_plus > 0
+    interior = in_plus & (cnt_plus == cnt_all)
+    free = mesh.dirichlet == 0
+    I = np.flatnonzero(interior & free)
+    B = np.flatnonzero(in_plus & ~interior & free)
+    in_omega = np.bincount(tets[omega_t].ravel(), minlength=n) > 0
+    omega = np.flatnonzero(in_omega & free)
+    owned = np.flatnonzero(P & free)
+    if not np.all(interior[omega]):
+        raise ValueError("omega_i is not interior to omega_i^+ (need r_hops >= 1)")
+    return dict(i=i, I=I, B=B, omega=omega, owned=owned, plus_tets=plus_t,
+                omega_tets=omega_t)
+
+
+def all_subdomains(mesh, owner, r_hops):
+    adj = node_adjacency(mesh.tets, mesh.n_nodes)
+    n_sub = int(owner.max()) + 1
+    return [subdomain_sets(mesh, owner, i, r_hops, adj) for i in range(n_sub)]
+
+
+def interface_tets(mesh, owner):
+    """omega_0: elements shared by at least two subdomains omega_i, i.e. elements whose
+    vertices have at least two different owners (Sec. 6 step 3)."""
+    o = owner[mesh.tets]
+    return np.flatnonzero(np.any(o != o[:, :1], axis=1))
