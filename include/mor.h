@@ -1,0 +1,218 @@
+/*
+ * mor.h -- C ABI of the GB300 localized model-order-reduction library (libmor).
+ *
+ * Method: "Distributed finite element solution using model order reduction"
+ * (Gustafsson, Hannukainen, Kohonen).  The library runs the data-parallel part of the
+ * paper's three-step framework (Sec. 6) on one GPU:
+ *   step 1  mor_build_subdomains  overlapping subdomains and r-hop extensions (Sec. 3,
+ *                                 Sec. 6 step 1, Sec. 7.1 "r-hops")
+ *   step 2  mor_build_bases       optimal local bases (Sec. 4, Sec. 6 step 2 and
+ *                                 "Randomized numerical linear algebra")
+ *   step 3  mor_project           Q^T A Q by the interface-only product (Eq. (17), Sec. 6
+ *                                 step 3), then mor_solve_reduced (diagonally
+ *                                 preconditioned CG on the reduced system, Sec. 6 step 3)
+ * plus mor_lift (u~ = sum_i S_i Q_i x_i, Eq. (10) with Def. 3.1) and mor_energy_norm.
+ *
+ * Model problem: -div(k grad u) = 1 in Omega, u = 0 on the boundary, P1 tetrahedra
+ * (Sec. 2; a per-element coefficient k as in Sec. 7.2).
+ *
+ * Conventions
+ *   - Return value: MOR_OK (0) or a negative MOR_ERR_* code; mor_last_error() gives a
+ *     thread-local message for the last failing call on the calling thread.
+ *   - Pointers marked [host] are read only during the call.  Pointers marked [device]
+ *     are CUDA device pointers owned by the caller; those given to
+ *     mor_build_subdomains must stay valid until the handle is freed.
+ *   - Handles are opaque, owned by the library and released by mor_free_*.  They own
+ *     their device memory.
+ *   - stream: a cudaStream_t (NULL = legacy default stream).  Every call enqueues its
+ *     GPU work on that stream and returns after its own status is known (the call
+ *     synchronizes the stream when it needs a device-side status).
+ *   - Index arrays are int32 in row-major layout; floating point is IEEE binary64
+ *     unless stated otherwise.
+ */
+#ifndef MOR_H
+#define MOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MOR_OK 0
+#define MOR_ERR_ARG (-1)            /* invalid argument or size                        */
+#define MOR_ERR_BAD_MESH (-2)       /* element with non-positive volume, bad index     */
+#define MOR_ERR_OOM (-3)            /* device or host allocation failed                */
+#define MOR_ERR_NOT_CONVERGED (-4)  /* an iterative solve hit max_iter (results kept)  */
+#define MOR_ERR_CUDA (-6)           /* CUDA runtime or launch error                    */
+#define MOR_ERR_STATE (-7)          /* handle used in the wrong state                  */
+
+#define MOR_FP64 0   /* every local solve, Gram and eigensolve in binary64             */
+#define MOR_MIXED 1  /* binary32 CG sweeps with binary64 residual refinement; binary64
+                        small dense factorisations and reduced solve                    */
+
+typedef struct mor_subdomains_s mor_subdomains;
+typedef struct mor_bases_s mor_bases;
+typedef struct mor_reduced_s mor_reduced;
+
+/* A P1 tetrahedral mesh.  Host copies drive the index construction of step 1; device
+ * copies feed the numeric kernels.  Elements must be positively oriented
+ * (det[x1-x0, x2-x0, x3-x0] > 0); otherwise MOR_ERR_BAD_MESH. */
+typedef struct {
+  int64_t n_nodes;
+  int64_t n_tets;
+  const int32_t* tets;       /* [host]   n_tets x 4 vertex ids                          */
+  const uint8_t* dirichlet;  /* [host]   n_nodes, 1 = node on the Dirichlet boundary    */
+  const double* xyz_dev;     /* [device] n_nodes x 3 coordinates                        */
+  const int32_t* tets_dev;   /* [device] n_tets x 4, same content as tets               */
+  const double* kappa_dev;   /* [device] n_tets coefficient k_T > 0                     */
+} mor_mesh;
+
+/* Step 1 (Sec. 3, Sec. 6 step 1, Sec. 7.1).  owner[host, n_nodes] labels every node with
+ * its subdomain 0..n_sub-1 (the graph partition; every label must occur).  For each
+ * subdomain i: P_i = owned nodes; omega_i = elements touching P_i; the extension
+ * T_i^+ = elements touching the r_hops-hop ball of P_i in the edge graph of the mesh;
+ * I = free nodes of T_i^+ all of whose elements lie in T_i^+, B = its other free nodes.
+ * r_hops >= 1.  The mesh's device arrays are referenced, not copied. */
+int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
+                         void* stream, mor_subdomains** out);
+
+/* Sizes of step 1.  counts[host, n_sub x 6] receives per subdomain
+ * {|I|, |B|, |omega dofs|, |owned dofs|, |T_i^+|, |omega_i elements|}; n_sub_out may
+ * be NULL.  Pass counts = NULL to query n_sub only. */
+int mor_subdomains_counts(const mor_subdomains* h, int32_t* n_sub_out, int64_t* counts);
+
+/* Copy one index list of subdomain `sub` (global node ids, ascending) into out[host]:
+ * which = 0 I, 1 B, 2 omega dofs, 3 owned dofs, 4 T_i^+ element ids,
+ * 5 omega_i element ids.  The length is the matching entry of mor_subdomains_counts. */
+int mor_subdomains_indices(const mor_subdomains* h, int32_t sub, int32_t which,
+                           int32_t* out);
+
+#define MOR_SKETCH_FIELD 0 /* W = ((H^+)^{-1} L xi)_B, L L^T = H^+ element-wise       */
+
+typedef struct {
+  int32_t rank;        /* m: singular vectors kept per subdomain (fixed-rank mode)      */
+  int32_t oversample;  /* p: k = m + p sketch columns (Halko et al., App. B)           */
+  uint64_t seed;       /* Philox-4x32-10 key of the Gaussian draws                      */
+  int32_t precision;   /* MOR_FP64 or MOR_MIXED                                         */
+  int32_t sketch;      /* MOR_SKETCH_FIELD                                              */
+  double cg_rtol;      /* every local solve: ||b - A x||_2 <= cg_rtol ||b||_2 per column,
+                          residual measured in binary64                                 */
+  double inner_rtol;   /* MOR_MIXED: binary32 CG target per refinement sweep            */
+  int32_t max_iter;    /* CG iterations per sweep                                       */
+  int32_t max_refine;  /* refinement sweeps (MOR_FP64 uses them as restarts)            */
+  double sketch_rtol;  /* tolerance of the sketch solve W = ((H^+)^{-1} L xi)_B; W only
+                          has to be a Gaussian-like test matrix, so it may be loose
+                          (<= 0: use cg_rtol)                                           */
+  double tau;          /* diagonal-block update: drop eigen-directions of
+                          V^T A_ii V below tau * largest                                */
+  double orth_tol;     /* Gram orthonormalisation: drop directions below
+                          orth_tol * largest Gram eigenvalue                             */
+} mor_basis_opts;
+
+/* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
+ * inner_rtol 1e-4, max_iter 4000, max_refine 8, sketch_rtol 0, tau 1e-12,
+ * orth_tol 1e-14). */
+int mor_basis_opts_default(mor_basis_opts* opts);
+
+/* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (16)):
+ * assemble A_II, A_IB, H^+ on T_i^+ and H_i, A[P_i,P_i] on omega_i; solve
+ * A_II u_0 = b_I; sketch W (k columns, field mode); X = C_i A_II^{-1} A_IB W;
+ * orthonormalise X in the H_i inner product (R_i X^ = Qh); T = A_BI A_II^{-1} C_i^T H_i X^;
+ * G_B = T^T S_B^{-1} T with S_B^{-1} T from a solve with H^+ (Lemma 4.1), which equals
+ * B B^T for the matrix B of Eq. (16); eig(G_B) gives sigma_j^2 and the rotation of the
+ * top `rank` directions; V = D_i [u_0, X^ U_m]; Q_i = V W Lambda^{-1/2} from
+ * eig(V^T A[P_i,P_i] V) (so Q_i^T A_ii Q_i = I); b~_i = Q_i^T b[P_i].
+ * Returns MOR_ERR_NOT_CONVERGED (with the bases still built) if a local solve stopped
+ * at max_iter. */
+int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* opts, void* stream,
+                    mor_bases** out);
+
+/* Sizes of step 2: *kq = columns stored per subdomain (>= rank + 1, multiple of 4),
+ * *k = sketch columns; kept[host, n_sub] = basis columns kept per subdomain (may be
+ * NULL); *total_kept = sum of kept (may be NULL). */
+int mor_bases_info(const mor_bases* h, int32_t* kq, int32_t* k, int32_t* kept,
+                   int64_t* total_kept);
+
+/* sigma[host, n_sub x k]: the singular values of B (Eq. (16)) per subdomain, descending. */
+int mor_bases_sigma(const mor_bases* h, double* sigma);
+
+/* Q_i of subdomain `sub` into out[host, |owned| x kq] (row-major; rows = owned dofs in
+ * ascending node order, columns beyond kept[sub] are zero). */
+int mor_bases_get_Q(const mor_bases* h, int32_t sub, double* out);
+
+/* b~ for all subdomains into out[host, n_sub x kq]. */
+int mor_bases_get_bt(const mor_bases* h, double* out);
+
+/* Solver statistics of the last mor_build_bases: stats[host, 8] =
+ * {iterations of the four local solves (sketch, forward, adjoint, H^+), refinement
+ * sweeps (sum), columns not converged, 0, 0}. */
+int mor_bases_stats(const mor_bases* h, int64_t* stats);
+
+/* Step 3a (Eq. (17), Sec. 6 step 3): K~ with identity diagonal blocks (from step 2) and
+ * off-diagonal blocks K~_ij = Q_i^T A_0[P_i, P_j] Q_j, A_0 assembled on the interface
+ * elements omega_0 only, iterating over neighbouring pairs. */
+int mor_project(const mor_subdomains* sd, const mor_bases* b, void* stream,
+                mor_reduced** out);
+
+/* Reduced system sizes: *dim = n_sub * kq, *n_blocks = stored off-diagonal blocks. */
+int mor_reduced_info(const mor_reduced* h, int64_t* dim, int64_t* n_blocks);
+
+/* Dense copy of K~ into out[host, dim x dim] (for small systems; MOR_ERR_ARG if
+ * dim > 20000). */
+int mor_reduced_dense(const mor_reduced* h, double* out);
+
+typedef struct {
+  int32_t iterations;
+  int32_t converged;     /* 1 if ||b~ - K~ x|| <= rtol ||b~||                          */
+  double rel_residual;   /* final ||b~ - K~ x|| / ||b~|| (recursive residual)          */
+  double energy;         /* E = b~^T x                                                  */
+} mor_solve_info;
+
+/* Step 3b: K~ x = b~ by CG with the diagonal (= identity) preconditioner, binary64.
+ * x_dev [device, dim] is written.  info may be NULL. */
+int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void* stream,
+                      double* x_dev, mor_solve_info* info);
+
+/* u~ = sum_i S_i Q_i x_i on all nodes (zero on the Dirichlet boundary):
+ * x_dev [device, dim], u_dev [device, n_nodes]. */
+int mor_lift(const mor_subdomains* sd, const mor_bases* b, const double* x_dev,
+             double* u_dev, void* stream);
+
+/* ||u1 - u2||_A = sqrt(sum_T (u1-u2)_T^T K_T (u1-u2)_T) over all elements; u1_dev,
+ * u2_dev [device, n_nodes]; u2_dev may be NULL (then ||u1||_A).  *out [host]. */
+int mor_energy_norm(const mor_subdomains* sd, const double* u1_dev, const double* u2_dev,
+                    double* out, void* stream);
+
+/* Debug/parity access: the field-sketch right-hand side L xi of subdomain `sub`
+ * (rows I then B, k columns, row-major) into out[host, (|I|+|B|) x k], computed by the
+ * same kernel mor_build_bases uses (binary64 element factors). */
+int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts,
+                         int32_t sub, double* out, void* stream);
+
+/* Kernel timing for the roofline: when enabled, the three kernels of every local CG
+ * step of mor_build_bases are bracketed by CUDA events on the launching stream.
+ * mor_profile_query fills out[host, 4] = {launches, total milliseconds, algorithmic
+ * bytes moved, 0} accumulated since the last reset for `family` = 2 * kind + wide,
+ * kind 0 = sparse product q = A p with the p.q column sums, 1 = x/r update with the
+ * r.r and r.z sums, 2 = p update; wide 0 = binary32, 1 = binary64.  Algorithmic
+ * bytes count every stored nonzero (value + column index) and every vector block
+ * element the kernel must read or write once.  Process-wide state, not thread-safe. */
+int mor_profile_enable(int32_t on);
+int mor_profile_reset(void);
+int mor_profile_query(int32_t family, double* out);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (host-side counter), into *out. */
+int mor_kernel_launches(int64_t* out);
+
+void mor_free_subdomains(mor_subdomains* h);
+void mor_free_bases(mor_bases* h);
+void mor_free_reduced(mor_reduced* h);
+const char* mor_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOR_H */

@@ -1,0 +1,939 @@
+// C ABI of libmor (include/mor.h): handles, device memory, and the launch sequence of
+// the three steps of the paper's framework (Sec. 6) on one GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/mor.h"
+#include "mor_kernels.h"
+#include "mor_plan.h"
+
+using namespace mor;
+
+std::atomic<long long> mor::g_kernel_launches{0};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(expr)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(e_ == cudaErrorMemoryAllocation ? MOR_ERR_OOM : MOR_ERR_CUDA,      \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+#define TRY(expr)              \
+  do {                         \
+    int rc_ = (expr);          \
+    if (rc_ != MOR_OK) return rc_; \
+  } while (0)
+
+struct Allocs {
+  std::vector<void*> ptrs;
+  Allocs() = default;
+  Allocs(const Allocs&) = delete;
+  Allocs& operator=(const Allocs&) = delete;
+  ~Allocs() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  int alloc(T** p, size_t n, bool zero = true, cudaStream_t st = nullptr) {
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? MOR_ERR_OOM : MOR_ERR_CUDA,
+                  std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    ptrs.push_back(*p);
+    if (zero) {
+      e = cudaMemsetAsync(*p, 0, n * sizeof(T), st);
+      if (e != cudaSuccess) return fail(MOR_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return MOR_OK;
+  }
+  template <class T>
+  int upload(T** p, const std::vector<T>& h, cudaStream_t st) {
+    TRY(alloc(p, h.size(), false));
+    if (!h.empty()) {
+      cudaError_t e = cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T),
+                                      cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return fail(MOR_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return MOR_OK;
+  }
+};
+
+int upload_tiles(Allocs& A, const HostTiles& h, DTiles& d, cudaStream_t st) {
+  int32_t *sd, *r0, *r1, *lo, *hi;
+  TRY(A.upload(&sd, h.sd, st));
+  TRY(A.upload(&r0, h.r0, st));
+  TRY(A.upload(&r1, h.r1, st));
+  TRY(A.upload(&lo, h.lo, st));
+  TRY(A.upload(&hi, h.hi, st));
+  d.n = (int)h.sd.size();
+  d.sd = sd;
+  d.r0 = r0;
+  d.r1 = r1;
+  d.lo = lo;
+  d.hi = hi;
+  return MOR_OK;
+}
+
+// ---- kernel timing (roofline) ------------------------------------------------------
+// family = 2 * kind + wide (kind 0 sparse product, 1 x/r update, 2 p update)
+constexpr int kFamilies = 6;
+struct Prof {
+  bool on = false;
+  double launches[kFamilies] = {}, ms[kFamilies] = {}, bytes[kFamilies] = {};
+  std::vector<std::array<cudaEvent_t, 4>> pool;
+  struct Pending {
+    int wide;
+    double bytes[3];
+    size_t ev;
+  };
+  std::vector<Pending> pending;
+  size_t used = 0;
+  const cudaEvent_t* take() {
+    if (used == pool.size()) {
+      std::array<cudaEvent_t, 4> e;
+      for (auto& x : e) cudaEventCreate(&x);
+      pool.push_back(e);
+    }
+    return pool[used++].data();
+  }
+  void collect() {
+    for (auto& p : pending)
+      for (int kind = 0; kind < 3; ++kind) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pool[p.ev][kind], pool[p.ev][kind + 1]) == cudaSuccess) {
+          int f = 2 * kind + p.wide;
+          launches[f] += 1;
+          ms[f] += t;
+          bytes[f] += p.bytes[kind];
+        }
+      }
+    pending.clear();
+    used = 0;
+  }
+};
+Prof g_prof;
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int round_up4(int x) { return (x + 3) & ~3; }
+
+}  // namespace
+
+// ======================================================================================
+struct mor_subdomains_s {
+  HostPlan hp;
+  Allocs mem;
+  const double* xyz = nullptr;
+  const int32_t* tets = nullptr;
+  const double* kappa = nullptr;
+  int32_t *p_node, *p_sd, *w_node, *w_sd, *w2p, *w2o, *o2w, *o_node, *o_sd;
+  uint8_t* p_isB;
+  int32_t *patP_col, *patP_w, *patW_col, *patW_w;
+  int64_t *incP_ptr, *incW_ptr;
+  int32_t *incP_tet, *incW_tet;
+  uint32_t *incP_code, *incW_code;
+  DTiles tP_all, tP_I, tP_B, tW, tO;
+  int64_t* pair_ptr;
+  int32_t *e_urow, *e_vrow, *e_unode, *e_vnode;
+  int64_t* n2t_ptr;
+  int32_t* n2t;
+  std::vector<int32_t> nbr_ptr, nbr_sd, nbr_blk;
+  int64_t n_iface = 0;
+  int max_tiles = 0;
+};
+
+struct mor_bases_s {
+  int n_sd = 0, k = 0, kp = 0, kq = 0, m = 0;
+  Allocs mem;
+  double *Q = nullptr, *bt = nullptr, *sigma = nullptr;
+  int* kept = nullptr;
+  std::vector<int32_t> h_kept;
+  std::vector<double> h_sigma;
+  std::vector<int64_t> Ooff;
+  int64_t stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+struct mor_reduced_s {
+  int n_sd = 0, kq = 0, n_pairs = 0;
+  int64_t dim = 0;
+  Allocs mem;
+  double* blocks = nullptr;
+  double* bt = nullptr;
+  int32_t *nbr_ptr, *nbr_sd, *nbr_blk;
+  std::vector<int32_t> h_nbr_ptr, h_nbr_sd, h_nbr_blk;
+};
+
+// ======================================================================================
+extern "C" {
+
+const char* mor_last_error(void) { return g_err.c_str(); }
+
+int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
+                         void* stream, mor_subdomains** out) {
+  if (!mesh || !owner || !out) return fail(MOR_ERR_ARG, "mor_build_subdomains: null argument");
+  if (!mesh->xyz_dev || !mesh->tets_dev || !mesh->kappa_dev)
+    return fail(MOR_ERR_ARG, "mor_build_subdomains: null device mesh array");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto h = std::make_unique<mor_subdomains_s>();
+  std::string err;
+  int rc = build_host_plan(mesh->n_nodes, mesh->n_tets, mesh->tets, mesh->dirichlet, owner,
+                           r_hops, h->hp, err);
+  if (rc != MOR_OK) return fail(rc, err);
+  const HostPlan& hp = h->hp;
+  h->xyz = mesh->xyz_dev;
+  h->tets = mesh->tets_dev;
+  h->kappa = mesh->kappa_dev;
+  Allocs& A = h->mem;
+  TRY(A.upload(&h->p_node, hp.p_node, st));
+  TRY(A.upload(&h->p_sd, hp.p_sd, st));
+  TRY(A.upload(&h->p_isB, hp.p_isB, st));
+  TRY(A.upload(&h->w_node, hp.w_node, st));
+  TRY(A.upload(&h->w_sd, hp.w_sd, st));
+  TRY(A.upload(&h->w2p, hp.w2p, st));
+  TRY(A.upload(&h->w2o, hp.w2o, st));
+  TRY(A.upload(&h->o2w, hp.o2w, st));
+  TRY(A.upload(&h->o_node, hp.o_node, st));
+  TRY(A.upload(&h->o_sd, hp.o_sd, st));
+  TRY(A.upload(&h->patP_col, hp.pat_P.col, st));
+  TRY(A.upload(&h->patP_w, hp.pat_P.width, st));
+  TRY(A.upload(&h->patW_col, hp.pat_W.col, st));
+  TRY(A.upload(&h->patW_w, hp.pat_W.width, st));
+  TRY(A.upload(&h->incP_ptr, hp.incP_ptr, st));
+  TRY(A.upload(&h->incW_ptr, hp.incW_ptr, st));
+  TRY(A.upload(&h->incP_tet, hp.incP_tet, st));
+  TRY(A.upload(&h->incW_tet, hp.incW_tet, st));
+  TRY(A.upload(&h->incP_code, hp.incP_code, st));
+  TRY(A.upload(&h->incW_code, hp.incW_code, st));
+  TRY(upload_tiles(A, hp.tP_all, h->tP_all, st));
+  TRY(upload_tiles(A, hp.tP_I, h->tP_I, st));
+  TRY(upload_tiles(A, hp.tP_B, h->tP_B, st));
+  TRY(upload_tiles(A, hp.tW, h->tW, st));
+  TRY(upload_tiles(A, hp.tO, h->tO, st));
+  TRY(A.upload(&h->pair_ptr, hp.pair_ptr, st));
+  TRY(A.upload(&h->e_urow, hp.e_urow, st));
+  TRY(A.upload(&h->e_vrow, hp.e_vrow, st));
+  TRY(A.upload(&h->e_unode, hp.e_unode, st));
+  TRY(A.upload(&h->e_vnode, hp.e_vnode, st));
+  TRY(A.upload(&h->n2t_ptr, hp.n2t_ptr, st));
+  TRY(A.upload(&h->n2t, hp.n2t, st));
+  h->n_iface = (int64_t)hp.e_urow.size();
+  h->max_tiles = std::max({h->tP_all.n, h->tW.n, h->tO.n, h->tP_B.n, 1});
+  // block-sparse neighbour structure of the reduced matrix: pair p gives blocks
+  // 2p = (i, j) and 2p + 1 = (j, i)
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> rows(hp.n_sd);
+  for (size_t p = 0; p < hp.pair_i.size(); ++p) {
+    rows[hp.pair_i[p]].emplace_back(hp.pair_j[p], (int32_t)(2 * p));
+    rows[hp.pair_j[p]].emplace_back(hp.pair_i[p], (int32_t)(2 * p + 1));
+  }
+  h->nbr_ptr.assign(1, 0);
+  for (auto& r : rows) {
+    std::sort(r.begin(), r.end());
+    for (auto& e : r) {
+      h->nbr_sd.push_back(e.first);
+      h->nbr_blk.push_back(e.second);
+    }
+    h->nbr_ptr.push_back((int32_t)h->nbr_sd.size());
+  }
+  CK(cudaStreamSynchronize(st));
+  *out = h.release();
+  return MOR_OK;
+}
+
+int mor_subdomains_counts(const mor_subdomains* h, int32_t* n_sub_out, int64_t* counts) {
+  if (!h) return fail(MOR_ERR_ARG, "mor_subdomains_counts: null handle");
+  if (n_sub_out) *n_sub_out = h->hp.n_sd;
+  if (counts)
+    for (int i = 0; i < h->hp.n_sd; ++i) {
+      const SubSets& s = h->hp.sets[i];
+      int64_t* c = counts + 6 * (int64_t)i;
+      c[0] = (int64_t)s.I.size();
+      c[1] = (int64_t)s.B.size();
+      c[2] = (int64_t)s.omega.size();
+      c[3] = (int64_t)s.owned.size();
+      c[4] = (int64_t)s.plus_tets.size();
+      c[5] = (int64_t)s.omega_tets.size();
+    }
+  return MOR_OK;
+}
+
+int mor_subdomains_indices(const mor_subdomains* h, int32_t sub, int32_t which, int32_t* out) {
+  if (!h || !out || sub < 0 || sub >= h->hp.n_sd || which < 0 || which > 5)
+    return fail(MOR_ERR_ARG, "mor_subdomains_indices: bad argument");
+  const SubSets& s = h->hp.sets[sub];
+  const std::vector<int32_t>* v[6] = {&s.I, &s.B, &s.omega, &s.owned, &s.plus_tets,
+                                      &s.omega_tets};
+  std::memcpy(out, v[which]->data(), v[which]->size() * sizeof(int32_t));
+  return MOR_OK;
+}
+
+int mor_basis_opts_default(mor_basis_opts* o) {
+  if (!o) return fail(MOR_ERR_ARG, "mor_basis_opts_default: null");
+  o->rank = 8;
+  o->oversample = 5;
+  o->seed = 0;
+  o->precision = MOR_MIXED;
+  o->sketch = MOR_SKETCH_FIELD;
+  o->cg_rtol = 1e-9;
+  o->inner_rtol = 1e-4;
+  o->max_iter = 4000;
+  o->max_refine = 8;
+  o->sketch_rtol = 0.0;
+  o->tau = 1e-12;
+  o->orth_tol = 1e-14;
+  return MOR_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================================
+namespace {
+
+// device matrices of one build
+struct Mat {
+  int32_t *width = nullptr, *col = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  int W = 0;
+  EllView<double> e64() const { return EllView<double>{width, col, v64, W}; }
+  EllView<float> e32() const { return EllView<float>{width, col, v32, W}; }
+};
+
+struct Build {
+  const mor_subdomains_s* S;
+  const mor_basis_opts* o;
+  cudaStream_t st;
+  Allocs mem;
+  int n_sd, k, kp, kq, m;
+  bool mixed;
+  // pinned poll word
+  int* h_poll = nullptr;
+  int* d_poll = nullptr;
+  // workspace
+  double *vR64 = nullptr;
+  void *xT = nullptr, *rT = nullptr, *pT = nullptr, *qT = nullptr, *bT = nullptr;
+  CgState cs{};
+  RefineState rs{};
+  int64_t iters[4] = {0, 0, 0, 0};
+  int64_t sweeps = 0, not_conv = 0;
+  ~Build() {
+    if (h_poll) cudaFreeHost(h_poll);
+  }
+
+  int poll(const int* active) {
+    launch_count_active(n_sd, active, d_poll, st);
+    CK(cudaMemcpyAsync(h_poll, d_poll, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return *h_poll;
+  }
+
+  template <typename T>
+  int solve(const DTiles& tl, const Mat& A, const T* dinvT, const double* b64, double* x64,
+            int nc, int which, double rtol) {
+    EllView<T> AT;
+    if constexpr (sizeof(T) == 4)
+      AT = A.e32();
+    else
+      AT = A.e64();
+    T* x = (T*)xT;
+    T* r = (T*)rT;
+    T* p = (T*)pT;
+    T* q = (T*)qT;
+    T* b = (T*)bT;
+    double rtol2 = rtol * rtol;
+    double itol = mixed ? std::min(o->inner_rtol, rtol) : 0.1 * rtol;
+    double itol2 = itol * itol;
+    double pb[3] = {0, 0, 0};
+    if (g_prof.on) prof_bytes(tl, A, sizeof(T), pb);
+    launch_zero_rows(tl, x64, kp, st);
+    for (int sweep = 0;; ++sweep) {
+      launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, rtol2, sweep == 0 ? 1 : 0, rs, st);
+      int act = poll(rs.active);
+      if (act < 0) return fail(MOR_ERR_CUDA, "poll failed");
+      if (act == 0) break;
+      if (sweep >= o->max_refine) {
+        not_conv += act;
+        break;
+      }
+      launch_cast_scale<T>(tl, vR64, b, kp, rs, st);
+      launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, cs, st);
+      int it = 0;
+      const int check = 8;
+      while (it < o->max_iter) {
+        int chunk = std::min(check, o->max_iter - it);
+        for (int c = 0; c < chunk; ++c) {
+          const cudaEvent_t* ev = nullptr;
+          if (g_prof.on) {
+            ev = g_prof.take();
+            g_prof.pending.push_back(
+                Prof::Pending{sizeof(T) == 4 ? 0 : 1, {pb[0], pb[1], pb[2]}, g_prof.used - 1});
+          }
+          launch_cg_step<T>(tl, AT, x, r, p, q, dinvT, kp, itol2, cs, st, ev);
+        }
+        it += chunk;
+        if (poll(cs.active) == 0) break;
+      }
+      iters[which] += it;
+      ++sweeps;
+      launch_accumulate<T>(tl, x, x64, kp, rs, st);
+    }
+    CK(cudaGetLastError());
+    return MOR_OK;
+  }
+
+  // algorithmic bytes of the three kernels of one CG step on the rows of tl:
+  // sparse product = every stored nonzero (value + column index) once + read p and
+  // write q once; x/r update = read x, r, p, q and write x, r (+ the diagonal);
+  // p update = read r, p and write p (+ the diagonal)
+  std::vector<double> nnz_by_mat;
+  const Mat* mats[8] = {};
+  double rows_of(const DTiles& tl) const;
+  void prof_bytes(const DTiles& tl, const Mat& A, size_t tsz, double out[3]) {
+    double nnz = 0;
+    for (int i = 0; i < 8; ++i)
+      if (mats[i] == &A) nnz = nnz_by_mat[i];
+    double rows = rows_of(tl);
+    out[0] = nnz * (tsz + 4.0) + rows * kp * tsz * 2.0;
+    out[1] = rows * kp * tsz * 6.0 + rows * tsz;
+    out[2] = rows * kp * tsz * 3.0 + rows * tsz;
+  }
+};
+
+double Build::rows_of(const DTiles& tl) const {
+  const HostPlan& hp = S->hp;
+  const HostTiles* ht = nullptr;
+  if (tl.sd == S->tP_I.sd) ht = &hp.tP_I;
+  else if (tl.sd == S->tP_all.sd) ht = &hp.tP_all;
+  else if (tl.sd == S->tP_B.sd) ht = &hp.tP_B;
+  else if (tl.sd == S->tW.sd) ht = &hp.tW;
+  else ht = &hp.tO;
+  double n = 0;
+  for (size_t t = 0; t < ht->r0.size(); ++t) n += ht->r1[t] - ht->r0[t];
+  return n;
+}
+
+__global__ void k_count_nnz(int64_t n, const int32_t* col, unsigned long long* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long c = (i < n && col[i] >= 0) ? 1ull : 0ull;
+  unsigned m = __ballot_sync(0xFFFFFFFFu, c != 0);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(out, (unsigned long long)__popc(m));
+}
+
+}  // namespace
+
+extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* opts,
+                               void* stream, mor_bases** out) {
+  if (!sd || !opts || !out) return fail(MOR_ERR_ARG, "mor_build_bases: null argument");
+  *out = nullptr;
+  const mor_basis_opts& o = *opts;
+  if (o.rank < 1 || o.oversample < 0)
+    return fail(MOR_ERR_ARG, "mor_build_bases: rank >= 1 and oversample >= 0 required");
+  int k = o.rank + o.oversample;
+  int kp = round_up4(k + 1);
+  int kq = round_up4(o.rank + 1);
+  if (kp > 80 || kq > 80)
+    return fail(MOR_ERR_ARG, "mor_build_bases: rank + oversample must be <= 79");
+  if (o.precision != MOR_FP64 && o.precision != MOR_MIXED)
+    return fail(MOR_ERR_ARG, "mor_build_bases: unknown precision");
+  if (o.sketch != MOR_SKETCH_FIELD) return fail(MOR_ERR_ARG, "mor_build_bases: unknown sketch");
+  if (!(o.cg_rtol > 0.0) || o.max_iter < 1 || o.max_refine < 1)
+    return fail(MOR_ERR_ARG, "mor_build_bases: bad solver tolerances");
+
+  cudaStream_t st = (cudaStream_t)stream;
+  const mor_subdomains_s& S = *sd;
+  const HostPlan& hp = S.hp;
+  Build B;
+  B.S = &S;
+  B.o = opts;
+  B.st = st;
+  B.n_sd = hp.n_sd;
+  B.k = k;
+  B.kp = kp;
+  B.kq = kq;
+  B.m = o.rank;
+  B.mixed = o.precision == MOR_MIXED;
+  Allocs& M = B.mem;
+  const int n_sd = hp.n_sd;
+  const int64_t nP = hp.nP, nW = hp.nW, nO = hp.nO;
+  const int WP = hp.pat_P.W, WW = hp.pat_W.W;
+  const int64_t nEllP = ceil_div(nP, 32) * 32 * WP;
+  const int64_t nEllW = ceil_div(nW, 32) * 32 * WW;
+  const int64_t nEllO = ceil_div(nO, 32) * 32 * WW;
+  const int64_t nIncP = (int64_t)hp.incP_tet.size();
+
+  CK(cudaMallocHost((void**)&B.h_poll, sizeof(int)));
+  TRY(M.alloc(&B.d_poll, 1, true, st));
+  int* d_err;
+  TRY(M.alloc(&d_err, 1, true, st));
+
+  // ---- assembly (Sec. 2, Sec. 4): A^+, H^+ on T_i^+; A, H_i on omega_i ----
+  double *valA_P, *valH_P, *loadP, *valA_W, *valH_W, *loadW;
+  TRY(M.alloc(&valA_P, nEllP, true, st));
+  TRY(M.alloc(&valH_P, nEllP, true, st));
+  TRY(M.alloc(&loadP, nP, true, st));
+  TRY(M.alloc(&valA_W, nEllW, true, st));
+  TRY(M.alloc(&valH_W, nEllW, true, st));
+  TRY(M.alloc(&loadW, nW, true, st));
+  launch_assemble(nP, S.incP_ptr, S.incP_tet, S.incP_code, WP, S.xyz, S.tets, S.kappa, valA_P,
+                  valH_P, loadP, d_err, st);
+  launch_assemble(nW, S.incW_ptr, S.incW_tet, S.incW_code, WW, S.xyz, S.tets, S.kappa, valA_W,
+                  valH_W, loadW, d_err, st);
+
+  // ---- extraction of the blocks used by the solves ----
+  auto make_mat = [&](Mat& mt, int64_t n_rows, int W, bool f32) -> int {
+    int64_t n = ceil_div(n_rows, 32) * 32 * W;
+    mt.W = W;
+    TRY(M.alloc(&mt.width, ceil_div(n_rows, 32), true, st));
+    TRY(M.alloc(&mt.col, n, false, st));
+    CK(cudaMemsetAsync(mt.col, 0xFF, n * sizeof(int32_t), st));
+    TRY(M.alloc(&mt.v64, n, true, st));
+    if (f32) TRY(M.alloc(&mt.v32, n, true, st));
+    return MOR_OK;
+  };
+  Mat A_II, A_IB, A_BI, Hp, Hi, App;
+  double *dA64, *dH64;
+  float *dA32, *dH32;
+  TRY(make_mat(A_II, nP, WP, true));
+  TRY(make_mat(A_IB, nP, WP, false));
+  TRY(make_mat(A_BI, nP, WP, false));
+  TRY(make_mat(Hp, nP, WP, true));
+  TRY(make_mat(Hi, nW, WW, false));
+  TRY(make_mat(App, nO, WW, false));
+  TRY(M.alloc(&dA64, nP, true, st));
+  TRY(M.alloc(&dH64, nP, true, st));
+  TRY(M.alloc(&dA32, nP, true, st));
+  TRY(M.alloc(&dH32, nP, true, st));
+  const double drop = 1e-12;  // structural zeros of the element stiffness (Kuhn split)
+  launch_extract(nP, nullptr, S.p_isB, 0, S.patP_col, S.patP_w, WP, valA_P, nullptr, S.p_isB, 0,
+                 drop, WP, A_II.width, A_II.col, A_II.v64, A_II.v32, dA64, dA32, st);
+  launch_extract(nP, nullptr, S.p_isB, 0, S.patP_col, S.patP_w, WP, valA_P, nullptr, S.p_isB, 1,
+                 drop, WP, A_IB.width, A_IB.col, A_IB.v64, nullptr, nullptr, nullptr, st);
+  launch_extract(nP, nullptr, S.p_isB, 1, S.patP_col, S.patP_w, WP, valA_P, nullptr, S.p_isB, 0,
+                 drop, WP, A_BI.width, A_BI.col, A_BI.v64, nullptr, nullptr, nullptr, st);
+  launch_extract(nP, nullptr, nullptr, 0, S.patP_col, S.patP_w, WP, valH_P, nullptr, nullptr, 0,
+                 -1.0, WP, Hp.width, Hp.col, Hp.v64, Hp.v32, dH64, dH32, st);
+  launch_extract(nW, nullptr, nullptr, 0, S.patW_col, S.patW_w, WW, valH_W, nullptr, nullptr, 0,
+                 -1.0, WW, Hi.width, Hi.col, Hi.v64, nullptr, nullptr, nullptr, st);
+  launch_extract(nO, S.o2w, nullptr, 0, S.patW_col, S.patW_w, WW, valA_W, S.w2o, nullptr, 0,
+                 drop, WW, App.width, App.col, App.v64, nullptr, nullptr, nullptr, st);
+  {
+    // nonzero counts for the algorithmic-bytes model of the timed kernels
+    unsigned long long* d_cnt;
+    TRY(M.alloc(&d_cnt, 2, true, st));
+    count_launch(2);
+    k_count_nnz<<<(unsigned)ceil_div(nEllP, 256), 256, 0, st>>>(nEllP, A_II.col, d_cnt);
+    k_count_nnz<<<(unsigned)ceil_div(nEllP, 256), 256, 0, st>>>(nEllP, Hp.col, d_cnt + 1);
+    unsigned long long hc[2];
+    CK(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    B.nnz_by_mat = {(double)hc[0], (double)hc[1]};
+    B.mats[0] = &A_II;
+    B.mats[1] = &Hp;
+  }
+  int h_err = 0;
+  CK(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h_err) return fail(MOR_ERR_BAD_MESH, "mor_build_bases: element with non-positive volume");
+
+  // ---- solver workspace ----
+  size_t tsz = B.mixed ? sizeof(float) : sizeof(double);
+  double *vS, *vG, *vF, *vX;
+  TRY(M.alloc(&vS, nP * kp, true, st));
+  TRY(M.alloc(&vG, nP * kp, true, st));
+  TRY(M.alloc(&vF, nP * kp, true, st));
+  TRY(M.alloc(&vX, nP * kp, true, st));
+  TRY(M.alloc(&B.vR64, nP * kp, true, st));
+  {
+    unsigned char *a, *b, *c, *d, *e;
+    TRY(M.alloc(&a, nP * kp * tsz, true, st));
+    TRY(M.alloc(&b, nP * kp * tsz, true, st));
+    TRY(M.alloc(&c, nP * kp * tsz, true, st));
+    TRY(M.alloc(&d, nP * kp * tsz, true, st));
+    TRY(M.alloc(&e, nP * kp * tsz, true, st));
+    B.xT = a;
+    B.rT = b;
+    B.pT = c;
+    B.qT = d;
+    B.bT = e;
+  }
+  int mt = S.max_tiles;
+  TRY(M.alloc(&B.cs.rz, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.bb, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.alpha, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.beta, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.done, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.part1, (size_t)mt * kp, true, st));
+  TRY(M.alloc(&B.cs.part2, (size_t)mt * kp, true, st));
+  TRY(M.alloc(&B.cs.counter, n_sd, true, st));
+  TRY(M.alloc(&B.cs.iters, n_sd, true, st));
+  TRY(M.alloc(&B.cs.active, n_sd, true, st));
+  TRY(M.alloc(&B.rs.obb, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.rs.orr, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.rs.scale, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.rs.part, (size_t)mt * kp, true, st));
+  TRY(M.alloc(&B.rs.counter, n_sd, true, st));
+  TRY(M.alloc(&B.rs.active, n_sd, true, st));
+  double *Xw, *Yw, *Zw, *u0w, *V, *AV, *bP;
+  TRY(M.alloc(&Xw, nW * kp, true, st));
+  TRY(M.alloc(&Yw, nW * kp, true, st));
+  TRY(M.alloc(&Zw, nW * kp, true, st));
+  TRY(M.alloc(&u0w, nW, true, st));
+  TRY(M.alloc(&V, nO * kq, true, st));
+  TRY(M.alloc(&AV, nO * kq, true, st));
+  TRY(M.alloc(&bP, nO, true, st));
+  double *G, *evals, *evecs, *Mm, *gpart;
+  int *gcnt, *kcnt;
+  TRY(M.alloc(&G, (size_t)n_sd * kp * kp, true, st));
+  TRY(M.alloc(&evals, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&evecs, (size_t)n_sd * kp * kp, true, st));
+  TRY(M.alloc(&Mm, (size_t)n_sd * kp * kp, true, st));
+  TRY(M.alloc(&gpart, (size_t)mt * kp * kp, true, st));
+  TRY(M.alloc(&gcnt, n_sd, true, st));
+  TRY(M.alloc(&kcnt, n_sd, true, st));
+
+  auto bases = std::make_unique<mor_bases_s>();
+  mor_bases_s& Bo = *bases;
+  Bo.n_sd = n_sd;
+  Bo.k = k;
+  Bo.kp = kp;
+  Bo.kq = kq;
+  Bo.m = o.rank;
+  Bo.Ooff = hp.Ooff;
+  TRY(Bo.mem.alloc(&Bo.Q, nO * kq, true, st));
+  TRY(Bo.mem.alloc(&Bo.bt, (size_t)n_sd * kq, true, st));
+  TRY(Bo.mem.alloc(&Bo.sigma, (size_t)n_sd * kp, true, st));
+  TRY(Bo.mem.alloc(&Bo.kept, n_sd, true, st));
+
+  auto solve = [&](const DTiles& tl, const Mat& A, bool isA, const double* b64, double* x64,
+                   int nc, int which, double rtol) -> int {
+    if (B.mixed) return B.solve<float>(tl, A, isA ? dA32 : dH32, b64, x64, nc, which, rtol);
+    return B.solve<double>(tl, A, isA ? dA64 : dH64, b64, x64, nc, which, rtol);
+  };
+  const double rt = o.cg_rtol;
+  const double rt_sketch = o.sketch_rtol > 0.0 ? o.sketch_rtol : o.cg_rtol;
+
+  // ---- sketch: W = ((H^+)^{-1} L xi)_B ----
+  double* lrow;
+  TRY(M.alloc(&lrow, nIncP * 4, false, st));
+  launch_elem_lrow(nIncP, S.incP_tet, S.incP_code, S.xyz, S.tets, lrow, st);
+  launch_sketch_rhs(B.mixed, 0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lrow, k, o.seed,
+                    vS, kp, st);
+  TRY(solve(S.tP_all, Hp, false, vS, vG, k, 0, rt_sketch));
+
+  // ---- forward solve A_II [X | u_0] = [A_IB W | b_I] (Prob. 4 and the lifting) ----
+  launch_spmm<double>(S.tP_I, A_IB.e64(), vG, vF, kp, st);
+  launch_set_col(S.tP_I, loadP, vF, kp, k, st);
+  TRY(solve(S.tP_I, A_II, true, vF, vX, k + 1, 1, rt));
+
+  // ---- X = C_i X_full, orthonormalise in the H_i inner product (twice) ----
+  launch_gather_rows(nW, S.w2p, vX, kp, 0, Xw, kp, 0, kp, st);
+  launch_gather_rows(nW, S.w2p, vX, kp, k, u0w, 1, 0, 1, st);
+  for (int pass = 0; pass < 2; ++pass) {
+    launch_spmm<double>(S.tW, Hi.e64(), Xw, Yw, kp, st);
+    launch_gram(S.tW, n_sd, Xw, kp, k, Yw, kp, k, gpart, gcnt, G, kp, st);
+    launch_sym_eig(n_sd, G, kp, k, evals, evecs, st);
+    launch_make_M(n_sd, 0, evals, evecs, kp, k, o.orth_tol, 0, Mm, kcnt, st);
+    launch_rowmul(S.tW, Xw, kp, k, Mm, kp, Zw, kp, k, st);
+    std::swap(Xw, Zw);
+  }
+
+  // ---- adjoint: T = A_BI A_II^{-1} C_i^T H_i X^ (two left solves, Eq. (16)) ----
+  launch_spmm<double>(S.tW, Hi.e64(), Xw, Yw, kp, st);
+  CK(cudaMemsetAsync(vF, 0, nP * kp * sizeof(double), st));
+  launch_scatter_rows(nW, S.w2p, Yw, kp, vF, kp, kp, st);
+  TRY(solve(S.tP_I, A_II, true, vF, vX, k, 2, rt));
+  CK(cudaMemsetAsync(vS, 0, nP * kp * sizeof(double), st));
+  launch_spmm<double>(S.tP_B, A_BI.e64(), vX, vS, kp, st);
+  // S_B^{-1} T = ((H^+)^{-1} [0; T])_B  (Lemma 4.1 / block inverse of H^+)
+  TRY(solve(S.tP_all, Hp, false, vS, vG, k, 3, rt));
+  launch_gram(S.tP_B, n_sd, vS, kp, k, vG, kp, k, gpart, gcnt, G, kp, st);
+  // eig(G_B) = sigma_j^2 (kept on the device as squares); the rotation of the top
+  // `rank` directions gives the basis X^ U_m = R_i^{-1} Qh U_m
+  launch_sym_eig(n_sd, G, kp, k, Bo.sigma, evecs, st);
+  launch_make_M(n_sd, 1, Bo.sigma, evecs, kp, k, 0.0, o.rank, Mm, kcnt, st);
+  launch_rowmul(S.tW, Xw, kp, k, Mm, kp, Zw, kp, o.rank, st);
+
+  // ---- V = D_i [u_0, X^ U_m], diagonal-block update Q_i = V W Lambda^{-1/2} ----
+  launch_gather_rows(nO, S.o2w, u0w, 1, 0, V, kq, 0, 1, st);
+  launch_gather_rows(nO, S.o2w, Zw, kp, 0, V, kq, 1, o.rank, st);
+  launch_spmm<double>(S.tO, App.e64(), V, AV, kq, st);
+  launch_gram(S.tO, n_sd, V, kq, o.rank + 1, AV, kq, o.rank + 1, gpart, gcnt, G, kq, st);
+  launch_sym_eig(n_sd, G, kq, o.rank + 1, evals, evecs, st);
+  launch_make_M(n_sd, 0, evals, evecs, kq, o.rank + 1, o.tau, 0, Mm, Bo.kept, st);
+  launch_rowmul(S.tO, V, kq, o.rank + 1, Mm, kq, Bo.Q, kq, o.rank + 1, st);
+  // b~_i = Q_i^T b[P_i]
+  launch_gather_rows(nO, S.o2w, loadW, 1, 0, bP, 1, 0, 1, st);
+  launch_gram(S.tO, n_sd, Bo.Q, kq, kq, bP, 1, 1, gpart, gcnt, Bo.bt, kq, st);
+  CK(cudaGetLastError());
+
+  Bo.h_kept.resize(n_sd);
+  Bo.h_sigma.resize((size_t)n_sd * kp);
+  CK(cudaMemcpyAsync(Bo.h_kept.data(), Bo.kept, n_sd * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(Bo.h_sigma.data(), Bo.sigma, (size_t)n_sd * kp * sizeof(double),
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (auto& s : Bo.h_sigma) s = std::sqrt(std::max(s, 0.0));
+  if (g_prof.on) g_prof.collect();
+  Bo.stats[0] = B.iters[0];
+  Bo.stats[1] = B.iters[1];
+  Bo.stats[2] = B.iters[2];
+  Bo.stats[3] = B.iters[3];
+  Bo.stats[4] = B.sweeps;
+  Bo.stats[5] = B.not_conv;
+  *out = bases.release();
+  if (B.not_conv > 0)
+    return fail(MOR_ERR_NOT_CONVERGED, "mor_build_bases: " + std::to_string(B.not_conv) +
+                                           " local solve columns did not converge");
+  return MOR_OK;
+}
+
+extern "C" {
+
+int mor_bases_info(const mor_bases* h, int32_t* kq, int32_t* k, int32_t* kept,
+                   int64_t* total_kept) {
+  if (!h) return fail(MOR_ERR_ARG, "mor_bases_info: null handle");
+  if (kq) *kq = h->kq;
+  if (k) *k = h->k;
+  int64_t tot = 0;
+  for (int i = 0; i < h->n_sd; ++i) {
+    if (kept) kept[i] = h->h_kept[i];
+    tot += h->h_kept[i];
+  }
+  if (total_kept) *total_kept = tot;
+  return MOR_OK;
+}
+
+int mor_bases_sigma(const mor_bases* h, double* sigma) {
+  if (!h || !sigma) return fail(MOR_ERR_ARG, "mor_bases_sigma: null argument");
+  for (int i = 0; i < h->n_sd; ++i)
+    for (int j = 0; j < h->k; ++j) sigma[(int64_t)i * h->k + j] = h->h_sigma[(int64_t)i * h->kp + j];
+  return MOR_OK;
+}
+
+int mor_bases_get_Q(const mor_bases* h, int32_t sub, double* out) {
+  if (!h || !out || sub < 0 || sub >= h->n_sd) return fail(MOR_ERR_ARG, "mor_bases_get_Q: bad argument");
+  int64_t r0 = h->Ooff[sub], r1 = h->Ooff[sub + 1];
+  CK(cudaMemcpy(out, h->Q + r0 * h->kq, (r1 - r0) * h->kq * sizeof(double),
+                cudaMemcpyDeviceToHost));
+  return MOR_OK;
+}
+
+int mor_bases_get_bt(const mor_bases* h, double* out) {
+  if (!h || !out) return fail(MOR_ERR_ARG, "mor_bases_get_bt: null argument");
+  CK(cudaMemcpy(out, h->bt, (size_t)h->n_sd * h->kq * sizeof(double), cudaMemcpyDeviceToHost));
+  return MOR_OK;
+}
+
+int mor_bases_stats(const mor_bases* h, int64_t* stats) {
+  if (!h || !stats) return fail(MOR_ERR_ARG, "mor_bases_stats: null argument");
+  for (int i = 0; i < 8; ++i) stats[i] = h->stats[i];
+  return MOR_OK;
+}
+
+int mor_project(const mor_subdomains* sd, const mor_bases* b, void* stream, mor_reduced** out) {
+  if (!sd || !b || !out) return fail(MOR_ERR_ARG, "mor_project: null argument");
+  *out = nullptr;
+  if (b->n_sd != sd->hp.n_sd) return fail(MOR_ERR_STATE, "mor_project: bases of another plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  auto r = std::make_unique<mor_reduced_s>();
+  const HostPlan& hp = sd->hp;
+  r->n_sd = hp.n_sd;
+  r->kq = b->kq;
+  r->n_pairs = (int)hp.pair_i.size();
+  r->dim = (int64_t)hp.n_sd * b->kq;
+  Allocs& A = r->mem;
+  double* aval;
+  TRY(A.alloc(&aval, sd->n_iface, false, st));
+  launch_iface_vals(sd->n_iface, sd->e_unode, sd->e_vnode, sd->n2t_ptr, sd->n2t, sd->xyz,
+                    sd->tets, sd->kappa, aval, st);
+  TRY(A.alloc(&r->blocks, (size_t)2 * std::max(r->n_pairs, 1) * b->kq * b->kq, true, st));
+  launch_pair_blocks(r->n_pairs, sd->pair_ptr, sd->e_urow, sd->e_vrow, aval, b->Q, b->kq,
+                     r->blocks, st);
+  TRY(A.alloc(&r->bt, r->dim, false, st));
+  CK(cudaMemcpyAsync(r->bt, b->bt, r->dim * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  r->h_nbr_ptr = sd->nbr_ptr;
+  r->h_nbr_sd = sd->nbr_sd;
+  r->h_nbr_blk = sd->nbr_blk;
+  TRY(A.upload(&r->nbr_ptr, r->h_nbr_ptr, st));
+  TRY(A.upload(&r->nbr_sd, r->h_nbr_sd, st));
+  TRY(A.upload(&r->nbr_blk, r->h_nbr_blk, st));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  *out = r.release();
+  return MOR_OK;
+}
+
+int mor_reduced_info(const mor_reduced* h, int64_t* dim, int64_t* n_blocks) {
+  if (!h) return fail(MOR_ERR_ARG, "mor_reduced_info: null handle");
+  if (dim) *dim = h->dim;
+  if (n_blocks) *n_blocks = 2 * (int64_t)h->n_pairs;
+  return MOR_OK;
+}
+
+int mor_reduced_dense(const mor_reduced* h, double* out) {
+  if (!h || !out) return fail(MOR_ERR_ARG, "mor_reduced_dense: null argument");
+  if (h->dim > 20000) return fail(MOR_ERR_ARG, "mor_reduced_dense: system too large");
+  int kq = h->kq;
+  std::vector<double> blk((size_t)2 * h->n_pairs * kq * kq);
+  if (!blk.empty())
+    CK(cudaMemcpy(blk.data(), h->blocks, blk.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  std::memset(out, 0, (size_t)h->dim * h->dim * sizeof(double));
+  for (int64_t i = 0; i < h->dim; ++i) out[i * h->dim + i] = 1.0;
+  for (int i = 0; i < h->n_sd; ++i)
+    for (int q = h->h_nbr_ptr[i]; q < h->h_nbr_ptr[i + 1]; ++q) {
+      int j = h->h_nbr_sd[q];
+      const double* B = blk.data() + (size_t)h->h_nbr_blk[q] * kq * kq;
+      for (int a = 0; a < kq; ++a)
+        for (int c = 0; c < kq; ++c)
+          out[((int64_t)i * kq + a) * h->dim + (int64_t)j * kq + c] = B[a * kq + c];
+    }
+  return MOR_OK;
+}
+
+int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void* stream,
+                      double* x_dev, mor_solve_info* info) {
+  if (!h || !x_dev || !(rtol > 0.0) || max_iter < 1)
+    return fail(MOR_ERR_ARG, "mor_solve_reduced: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Allocs A;
+  RcgState s{};
+  s.x = x_dev;
+  TRY(A.alloc(&s.r, h->dim, false, st));
+  TRY(A.alloc(&s.p, h->dim, false, st));
+  TRY(A.alloc(&s.q, h->dim, false, st));
+  TRY(A.alloc(&s.part, (size_t)2 * h->n_sd, true, st));
+  TRY(A.alloc(&s.counter, 1, true, st));
+  TRY(A.alloc(&s.scal, 8, true, st));
+  TRY(A.alloc(&s.flag, 2, true, st));
+  launch_rcg_init(h->n_sd, h->kq, h->bt, s, st);
+  int hf[2] = {0, 0};
+  int it = 0;
+  while (it < max_iter) {
+    int chunk = std::min(16, max_iter - it);
+    for (int c = 0; c < chunk; ++c)
+      launch_rcg_step(h->n_sd, h->kq, h->nbr_ptr, h->nbr_sd, h->nbr_blk, h->blocks, rtol * rtol,
+                      s, st);
+    it += chunk;
+    CK(cudaMemcpyAsync(hf, s.flag, sizeof(hf), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hf[0]) break;
+  }
+  CK(cudaGetLastError());
+  double sc[8];
+  CK(cudaMemcpy(sc, s.scal, sizeof(sc), cudaMemcpyDeviceToHost));
+  // energy b~^T x
+  std::vector<double> hx(h->dim), hb(h->dim);
+  CK(cudaMemcpy(hx.data(), x_dev, h->dim * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(hb.data(), h->bt, h->dim * sizeof(double), cudaMemcpyDeviceToHost));
+  double E = 0.0;
+  for (int64_t i = 0; i < h->dim; ++i) E += hb[i] * hx[i];
+  if (info) {
+    info->iterations = hf[1];
+    info->converged = hf[0] && sc[4] <= rtol * rtol * sc[1];
+    info->rel_residual = sc[1] > 0 ? std::sqrt(sc[4] / sc[1]) : 0.0;
+    info->energy = E;
+  }
+  if (!(hf[0] && sc[4] <= rtol * rtol * sc[1]))
+    return fail(MOR_ERR_NOT_CONVERGED, "mor_solve_reduced: max_iter reached");
+  return MOR_OK;
+}
+
+int mor_lift(const mor_subdomains* sd, const mor_bases* b, const double* x_dev, double* u_dev,
+             void* stream) {
+  if (!sd || !b || !x_dev || !u_dev) return fail(MOR_ERR_ARG, "mor_lift: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(u_dev, 0, sd->hp.n_nodes * sizeof(double), st));
+  launch_lift(sd->hp.nO, sd->o_node, sd->o_sd, b->Q, b->kq, x_dev, u_dev, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return MOR_OK;
+}
+
+int mor_energy_norm(const mor_subdomains* sd, const double* u1_dev, const double* u2_dev,
+                    double* out, void* stream) {
+  if (!sd || !u1_dev || !out) return fail(MOR_ERR_ARG, "mor_energy_norm: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Allocs A;
+  double* part;
+  double* res;
+  int64_t nb = ceil_div(sd->hp.n_tets, 256);
+  TRY(A.alloc(&part, nb, false, st));
+  TRY(A.alloc(&res, 1, false, st));
+  launch_energy(sd->hp.n_tets, sd->xyz, sd->tets, sd->kappa, u1_dev, u2_dev, part, res, st);
+  double h = 0;
+  CK(cudaMemcpyAsync(&h, res, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *out = std::sqrt(std::max(h, 0.0));
+  return MOR_OK;
+}
+
+int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, int32_t sub,
+                         double* out, void* stream) {
+  if (!sd || !opts || !out || sub < 0 || sub >= sd->hp.n_sd)
+    return fail(MOR_ERR_ARG, "mor_debug_sketch_rhs: bad argument");
+  const HostPlan& hp = sd->hp;
+  cudaStream_t st = (cudaStream_t)stream;
+  int k = opts->rank + opts->oversample;
+  int64_t row0 = hp.Poff[sub], n_rows = hp.Poff[sub + 1] - row0;
+  int64_t nInc = (int64_t)hp.incP_tet.size();
+  Allocs A;
+  double *lrow, *res;
+  TRY(A.alloc(&lrow, nInc * 4, false, st));
+  TRY(A.alloc(&res, (hp.nP) * (size_t)k, true, st));
+  launch_elem_lrow(nInc, sd->incP_tet, sd->incP_code, sd->xyz, sd->tets, lrow, st);
+  launch_sketch_rhs(opts->precision == MOR_MIXED, row0, n_rows, sd->p_sd, sd->incP_ptr,
+                    sd->incP_tet, sd->incP_code, lrow, k, opts->seed, res, k, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, res + row0 * k, n_rows * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MOR_OK;
+}
+
+int mor_profile_enable(int32_t on) {
+  g_prof.on = on != 0;
+  return MOR_OK;
+}
+int mor_profile_reset(void) {
+  for (int f = 0; f < kFamilies; ++f) g_prof.launches[f] = g_prof.ms[f] = g_prof.bytes[f] = 0;
+  return MOR_OK;
+}
+int mor_profile_query(int32_t family, double* out) {
+  if (family < 0 || family >= kFamilies || !out)
+    return fail(MOR_ERR_ARG, "mor_profile_query: bad argument");
+  out[0] = g_prof.launches[family];
+  out[1] = g_prof.ms[family];
+  out[2] = g_prof.bytes[family];
+  out[3] = 0;
+  return MOR_OK;
+}
+int mor_kernel_launches(int64_t* out) {
+  if (!out) return fail(MOR_ERR_ARG, "mor_kernel_launches: null");
+  *out = (int64_t)g_kernel_launches.load();
+  return MOR_OK;
+}
+
+void mor_free_subdomains(mor_subdomains* h) { delete h; }
+void mor_free_bases(mor_bases* h) { delete h; }
+void mor_free_reduced(mor_reduced* h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Host launchers of the libmor CUDA kernels (one declaration per kernel family).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "mor_dev.cuh"
+
+namespace mor {
+
+// host-side count of kernel launches issued by the library (every launcher adds its
+// launches before enqueuing them)
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------- assembly (mor_assembly.cu) ----------------
+// Row-gather P1 assembly (Sec. 2, Sec. 4): for every row the element contributions
+// of its incident elements are summed in incidence order (deterministic): stiffness
+// k_T |T| grad(l_a).grad(l_b) into valA, H1 form |T| grad.grad + |T|(1+d_ab)/20
+// into valH, load |T|/4 into load[row].  err is set to 1 on det <= 0.
+void launch_assemble(int64_t n_rows, const int64_t* inc_ptr, const int32_t* inc_tet,
+                     const uint32_t* inc_code, int W, const double* xyz, const int32_t* tets,
+                     const double* kappa, double* valA, double* valH, double* load,
+                     int* err, cudaStream_t st);
+
+// Row a of the lower Cholesky factor of the element H1 matrix, for every incidence
+// entry (the element factors L_T of the field sketch, L L^T = H^+).
+void launch_elem_lrow(int64_t n_inc, const int32_t* inc_tet, const uint32_t* inc_code,
+                      const double* xyz, const int32_t* tets, double* lrow, cudaStream_t st);
+
+// out[r, j] = sum over incident elements T of (L_T xi_T[:, j])[a(r)], j < k, for rows
+// [row0, row0 + n_rows); xi from Philox counter (T, j, row_sd[r], 0).  fast = binary32
+// accumulation (the normals are identical either way).
+void launch_sketch_rhs(bool fast, int64_t row0, int64_t n_rows, const int32_t* row_sd,
+                       const int64_t* inc_ptr, const int32_t* inc_tet,
+                       const uint32_t* inc_code, const double* lrow, int k, uint64_t seed,
+                       double* out, int ld, cudaStream_t st);
+
+// Extract a sliced-ELL matrix from an assembled pattern: destination row r takes source
+// row s = row_src ? row_src[r] : r when row_cls is null or row_cls[s] == row_want;
+// an entry (s, c) is kept when (col_cls null or col_cls[c] == col_want), col_map is
+// null or col_map[c] >= 0, and |v| > drop_rel |v_ss| (drop_rel < 0 keeps all).
+// The kept columns are col_map[c] (or c).  Writes slice widths, columns, binary64 and
+// optional binary32 values, and optional inverse diagonals (Jacobi preconditioner).
+void launch_extract(int64_t n_dst, const int32_t* row_src, const uint8_t* row_cls,
+                    int row_want, const int32_t* src_col, const int32_t* src_width, int Wsrc,
+                    const double* src_val, const int32_t* col_map, const uint8_t* col_cls,
+                    int col_want, double drop_rel, int Wdst, int32_t* dst_width,
+                    int32_t* dst_col, double* dst_val, float* dst_val32, double* dinv64,
+                    float* dinv32, cudaStream_t st);
+
+// sum_T d_T^T K_T d_T, d = u1 - u2 (u2 may be null), over all elements; deterministic
+// two-level reduction into *out (device).  partials: ceil(n_tets/256) doubles.
+void launch_energy(int64_t n_tets, const double* xyz, const int32_t* tets,
+                   const double* kappa, const double* u1, const double* u2,
+                   double* partials, double* out, cudaStream_t st);
+
+// A[u, v] = sum over elements containing u and v of k_T |T| grad(l_u).grad(l_v)
+void launch_iface_vals(int64_t n_e, const int32_t* unode, const int32_t* vnode,
+                       const int64_t* n2t_ptr, const int32_t* n2t, const double* xyz,
+                       const int32_t* tets, const double* kappa, double* val,
+                       cudaStream_t st);
+
+// ---------------- sparse products and batched CG (mor_sparse.cu) ----------------
+struct CgState {
+  double *rz, *bb, *alpha, *beta;  // n_sd x kp
+  int* done;                        // n_sd x kp
+  double *part1, *part2;            // n_tiles x kp
+  int* counter;                     // n_sd
+  int* iters;                       // n_sd
+  int* active;                      // n_sd: active columns after the last update
+};
+
+template <typename T>
+struct EllView {
+  const int32_t* width;
+  const int32_t* col;
+  const T* val;
+  int W;
+};
+
+// Y = A X on the rows of `tiles` (kp columns, row stride kp).
+template <typename T>
+void launch_spmm(const DTiles& tiles, const EllView<T>& A, const T* X, T* Y, int kp,
+                 cudaStream_t st);
+
+// Jacobi-preconditioned CG, independent per (subdomain, column), one step = 3 kernels.
+template <typename T>
+void launch_cg_init(const DTiles& tiles, const T* b, T* x, T* r, T* p, const T* dinv,
+                    int kp, int nc, const CgState& s, cudaStream_t st);
+// ev (null or 4 events) is recorded before the sparse product and after each of the
+// three kernels of the step.
+template <typename T>
+void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, T* q,
+                    const T* dinv, int kp, double tol2, const CgState& s, cudaStream_t st,
+                    const cudaEvent_t* ev = nullptr);
+void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st);
+
+// iterative refinement: r64 = b64 - A64 x64 with per-column norms; scale = 1/||r64||
+// for columns with ||r64|| > rtol ||b64|| (0 otherwise); first = 1 records ||b64||.
+struct RefineState {
+  double *obb, *orr, *scale;  // n_sd x kp
+  double* part;               // n_tiles x kp
+  int* counter;               // n_sd
+  int* active;                // n_sd
+};
+void launch_residual64(const DTiles& tiles, const EllView<double>& A, const double* b64,
+                       const double* x64, double* r64, int kp, int nc, double rtol2,
+                       int first, const RefineState& s, cudaStream_t st);
+template <typename T>
+void launch_cast_scale(const DTiles& tiles, const double* r64, T* rT, int kp,
+                       const RefineState& s, cudaStream_t st);
+template <typename T>
+void launch_accumulate(const DTiles& tiles, const T* xT, double* x64, int kp,
+                       const RefineState& s, cudaStream_t st);
+void launch_zero_rows(const DTiles& tiles, double* x, int kp, cudaStream_t st);
+
+// ---------------- dense per-subdomain kernels (mor_dense.cu) ----------------
+// G[sd] = X^T Y over the rows of tiles: nx x ny with row stride ldg and subdomain
+// stride ldg*ldg, or for ny == 1 a vector with subdomain stride ldg.
+// part: n_tiles x nx x ny doubles.
+void launch_gram(const DTiles& tiles, int n_sd, const double* X, int ldx, int nx,
+                 const double* Y, int ldy, int ny, double* part, int* counter, double* G,
+                 int ldg, cudaStream_t st);
+// symmetric eigensolver (cyclic Jacobi, parallel ordering) per subdomain on the
+// leading n x n block of A[sd] (stride ld); evals descending (n_sd x ld), evecs
+// columns (n_sd x ld x ld).
+void launch_sym_eig(int n_sd, const double* A, int ld, int n, double* evals,
+                    double* evecs, cudaStream_t st);
+// M[sd] from an eigen-decomposition: mode 0: V_j / sqrt(l_j) for l_j > rel * l_0 (else 0
+// column); mode 1: V_j for j < keep; kept[sd] = number of nonzero columns.
+void launch_make_M(int n_sd, int mode, const double* evals, const double* evecs, int ld,
+                   int n, double rel, int keep, double* M, int* kept, cudaStream_t st);
+// Y[r, j] = sum_{l < nin} X[r, l] M[sd(r)][l, j] for j < nout; columns nout..ldy-1 of Y
+// are zeroed.
+void launch_rowmul(const DTiles& tiles, const double* X, int ldx, int nin, const double* M,
+                   int ldm, double* Y, int ldy, int nout, cudaStream_t st);
+// dst[r, dc0 + c] = src[map[r], sc0 + c] (map null: r), c < ncols
+void launch_gather_rows(int64_t n_rows, const int32_t* map, const double* src, int lds,
+                        int sc0, double* dst, int ldd, int dc0, int ncols, cudaStream_t st);
+// dst[map[r], c] = src[r, c]
+void launch_scatter_rows(int64_t n_rows, const int32_t* map, const double* src, int lds,
+                         double* dst, int ldd, int ncols, cudaStream_t st);
+// dst[r, col] = src[r] for the rows of tiles
+void launch_set_col(const DTiles& tiles, const double* src, double* dst, int ld, int col,
+                    cudaStream_t st);
+void launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st);
+
+// ---------------- reduced system (mor_reduced.cu) ----------------
+// K~_ij = sum_e a_e Q[u_e]^T Q[v_e] per interface pair; block 2p = (i, j), 2p+1 = (j, i)
+void launch_pair_blocks(int n_pairs, const int64_t* pair_ptr, const int32_t* urow,
+                        const int32_t* vrow, const double* aval, const double* Q, int kq,
+                        double* blocks, cudaStream_t st);
+struct RcgState {
+  double *x, *r, *p, *q;    // dim
+  double* part;             // n_sd x 2
+  int* counter;             // 1
+  double* scal;             // [0] rz, [1] bb, [2] alpha, [3] beta, [4] rr
+  int* flag;                // [0] done, [1] iterations
+};
+void launch_rcg_init(int n_sd, int kq, const double* bt, const RcgState& s,
+                     cudaStream_t st);
+void launch_rcg_step(int n_sd, int kq, const int32_t* nbr_ptr, const int32_t* nbr_sd,
+                     const int32_t* nbr_blk, const double* blocks, double tol2,
+                     const RcgState& s, cudaStream_t st);
+void launch_lift(int64_t n_o, const int32_t* o_node, const int32_t* o_sd, const double* Q,
+                 int kq, const double* x, double* u, cudaStream_t st);
+
+}  // namespace mor
