@@ -205,8 +205,7 @@ def ours(args):
     sd = mor.Subdomains(gm, owner, p["r_hops"])
     a1_ms = 1e3 * (time.perf_counter() - t0)
     mixed = mor.basis_opts(rank=p["rank"], oversample=p["oversample"], seed=p["seed"],
-                           precision="mixed", cg_rtol=1e-8, inner_rtol=1e-4,
-                           sketch_rtol=1e-4)
+                           precision="mixed", cg_rtol=1e-9)
     fp64 = mor.basis_opts(rank=p["rank"], oversample=p["oversample"], seed=p["seed"],
                           precision="fp64", cg_rtol=1e-10)
 

@@ -49,8 +49,8 @@ extern "C" {
 #define MOR_ERR_STATE (-7)          /* handle used in the wrong state                  */
 
 #define MOR_FP64 0   /* every local solve, Gram and eigensolve in binary64             */
-#define MOR_MIXED 1  /* binary32 CG sweeps with binary64 residual refinement; binary64
-                        small dense factorisations and reduced solve                    */
+#define MOR_MIXED 1  /* binary32 CG recursions with binary64 residual replacement;
+                        binary64 small dense factorisations and reduced solve           */
 
 typedef struct mor_subdomains_s mor_subdomains;
 typedef struct mor_bases_s mor_bases;
@@ -99,9 +99,10 @@ typedef struct {
   int32_t sketch;      /* MOR_SKETCH_FIELD                                              */
   double cg_rtol;      /* every local solve: ||b - A x||_2 <= cg_rtol ||b||_2 per column,
                           residual measured in binary64                                 */
-  double inner_rtol;   /* MOR_MIXED: binary32 CG target per refinement sweep            */
-  int32_t max_iter;    /* CG iterations per sweep                                       */
-  int32_t max_refine;  /* refinement sweeps (MOR_FP64 uses them as restarts)            */
+  int32_t max_iter;    /* CG iterations per local solve                                 */
+  int32_t replace_every; /* the CG residual is replaced by the binary64 residual
+                          b - A x every replace_every iterations (rounded to a multiple
+                          of 8) and whenever the recursion reports convergence         */
   double sketch_rtol;  /* tolerance of the sketch solve W = ((H^+)^{-1} L xi)_B; W only
                           has to be a Gaussian-like test matrix, so it may be loose
                           (<= 0: use cg_rtol)                                           */
@@ -112,8 +113,7 @@ typedef struct {
 } mor_basis_opts;
 
 /* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
- * inner_rtol 1e-4, max_iter 4000, max_refine 8, sketch_rtol 0, tau 1e-12,
- * orth_tol 1e-14). */
+ * max_iter 20000, replace_every 40, sketch_rtol 0, tau 1e-12, orth_tol 1e-14). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 
 /* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (16)):
@@ -146,8 +146,8 @@ int mor_bases_get_Q(const mor_bases* h, int32_t sub, double* out);
 int mor_bases_get_bt(const mor_bases* h, double* out);
 
 /* Solver statistics of the last mor_build_bases: stats[host, 8] =
- * {iterations of the four local solves (sketch, forward, adjoint, H^+), refinement
- * sweeps (sum), columns not converged, 0, 0}. */
+ * {iterations of the four local solves (sketch, forward, adjoint, H^+), residual
+ * replacements (sum), columns not converged, 0, 0}. */
 int mor_bases_stats(const mor_bases* h, int64_t* stats);
 
 /* Step 3a (Eq. (17), Sec. 6 step 3): K~ with identity diagonal blocks (from step 2) and

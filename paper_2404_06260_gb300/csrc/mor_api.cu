@@ -6,6 +6,8 @@
 #include <array>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -295,9 +297,8 @@ int mor_basis_opts_default(mor_basis_opts* o) {
   o->precision = MOR_MIXED;
   o->sketch = MOR_SKETCH_FIELD;
   o->cg_rtol = 1e-9;
-  o->inner_rtol = 1e-4;
-  o->max_iter = 4000;
-  o->max_refine = 8;
+  o->max_iter = 20000;
+  o->replace_every = 40;
   o->sketch_rtol = 0.0;
   o->tau = 1e-12;
   o->orth_tol = 1e-14;
@@ -336,6 +337,7 @@ struct Build {
   RefineState rs{};
   int64_t iters[4] = {0, 0, 0, 0};
   int64_t sweeps = 0, not_conv = 0;
+  bool debug = getenv("MOR_DEBUG") != nullptr;
   ~Build() {
     if (h_poll) cudaFreeHost(h_poll);
   }
@@ -361,42 +363,61 @@ struct Build {
     T* q = (T*)qT;
     T* b = (T*)bT;
     double rtol2 = rtol * rtol;
-    double itol = mixed ? std::min(o->inner_rtol, rtol) : 0.1 * rtol;
-    double itol2 = itol * itol;
     double pb[3] = {0, 0, 0};
     if (g_prof.on) prof_bytes(tl, A, sizeof(T), pb);
+    // one CG per (subdomain, column) in precision T on the full system, with the
+    // recursively updated residual replaced by the binary64 residual b - A x64 every
+    // replace_every iterations and whenever the recursion reports convergence
+    // (residual replacement keeps the search directions, so no Krylov restart)
     launch_zero_rows(tl, x64, kp, st);
-    for (int sweep = 0;; ++sweep) {
-      launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, rtol2, sweep == 0 ? 1 : 0, rs, st);
-      int act = poll(rs.active);
-      if (act < 0) return fail(MOR_ERR_CUDA, "poll failed");
-      if (act == 0) break;
-      if (sweep >= o->max_refine) {
-        not_conv += act;
-        break;
-      }
-      launch_cast_scale<T>(tl, vR64, b, kp, rs, st);
-      launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, cs, st);
-      int it = 0;
-      const int check = 8;
-      while (it < o->max_iter) {
-        int chunk = std::min(check, o->max_iter - it);
-        for (int c = 0; c < chunk; ++c) {
-          const cudaEvent_t* ev = nullptr;
-          if (g_prof.on) {
-            ev = g_prof.take();
-            g_prof.pending.push_back(
-                Prof::Pending{sizeof(T) == 4 ? 0 : 1, {pb[0], pb[1], pb[2]}, g_prof.used - 1});
-          }
-          launch_cg_step<T>(tl, AT, x, r, p, q, dinvT, kp, itol2, cs, st, ev);
+    launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, rtol2, 1, rs, st);
+    if (poll(rs.active) == 0) return MOR_OK;
+    launch_cast<T>(tl, vR64, b, kp, st);
+    launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, cs, st);
+    const int check = 8;
+    const int every = std::max(check, o->replace_every / check * check);
+    int it = 0;
+    while (true) {
+      int chunk = std::min(check, o->max_iter - it);
+      for (int c = 0; c < chunk; ++c) {
+        const cudaEvent_t* ev = nullptr;
+        if (g_prof.on) {
+          ev = g_prof.take();
+          g_prof.pending.push_back(
+              Prof::Pending{sizeof(T) == 4 ? 0 : 1, {pb[0], pb[1], pb[2]}, g_prof.used - 1});
         }
-        it += chunk;
-        if (poll(cs.active) == 0) break;
+        launch_cg_step<T>(tl, AT, x, r, p, q, dinvT, kp, rtol2, cs, st, ev);
       }
-      iters[which] += it;
-      ++sweeps;
-      launch_accumulate<T>(tl, x, x64, kp, rs, st);
+      it += chunk;
+      int act = poll(cs.active);
+      if (act == 0 || it % every == 0 || it >= o->max_iter) {
+        launch_accum_reset<T>(tl, x, x64, kp, st);
+        launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, rtol2, 0, rs, st);
+        ++sweeps;
+        int ract = poll(rs.active);
+        if (debug) {
+          std::vector<double> orr((size_t)n_sd * kp), obb((size_t)n_sd * kp);
+          cudaMemcpy(orr.data(), rs.orr, orr.size() * sizeof(double), cudaMemcpyDeviceToHost);
+          cudaMemcpy(obb.data(), rs.obb, obb.size() * sizeof(double), cudaMemcpyDeviceToHost);
+          double worst = 0.0;
+          int wi = -1;
+          for (size_t i = 0; i < orr.size(); ++i)
+            if ((int)(i % kp) < nc && obb[i] > 0 && orr[i] / obb[i] > worst) {
+              worst = orr[i] / obb[i];
+              wi = (int)i;
+            }
+          fprintf(stderr, "[mor] solve %d it %d active %d recursive-active %d worst %.3e (sd %d col %d)\n",
+                  which, it, ract, act, std::sqrt(worst), wi / kp, wi % kp);
+        }
+        if (ract == 0) break;
+        if (it >= o->max_iter) {
+          not_conv += ract;
+          break;
+        }
+        launch_cg_replace<T>(tl, vR64, r, p, dinvT, kp, cs, rs, st);
+      }
     }
+    iters[which] += it;
     CK(cudaGetLastError());
     return MOR_OK;
   }
@@ -456,7 +477,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   if (o.precision != MOR_FP64 && o.precision != MOR_MIXED)
     return fail(MOR_ERR_ARG, "mor_build_bases: unknown precision");
   if (o.sketch != MOR_SKETCH_FIELD) return fail(MOR_ERR_ARG, "mor_build_bases: unknown sketch");
-  if (!(o.cg_rtol > 0.0) || o.max_iter < 1 || o.max_refine < 1)
+  if (!(o.cg_rtol > 0.0) || o.max_iter < 1 || o.replace_every < 1)
     return fail(MOR_ERR_ARG, "mor_build_bases: bad solver tolerances");
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -581,6 +602,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.alloc(&B.cs.bb, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.alpha, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.beta, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.rr, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.done, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.part1, (size_t)mt * kp, true, st));
   TRY(M.alloc(&B.cs.part2, (size_t)mt * kp, true, st));

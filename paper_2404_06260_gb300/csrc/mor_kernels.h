@@ -65,6 +65,7 @@ void launch_iface_vals(int64_t n_e, const int32_t* unode, const int32_t* vnode,
 // ---------------- sparse products and batched CG (mor_sparse.cu) ----------------
 struct CgState {
   double *rz, *bb, *alpha, *beta;  // n_sd x kp
+  double* rr;                       // n_sd x kp: recursive ||r||^2 after the last update
   int* done;                        // n_sd x kp
   double *part1, *part2;            // n_tiles x kp
   int* counter;                     // n_sd
@@ -97,8 +98,8 @@ void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, 
                     const cudaEvent_t* ev = nullptr);
 void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st);
 
-// iterative refinement: r64 = b64 - A64 x64 with per-column norms; scale = 1/||r64||
-// for columns with ||r64|| > rtol ||b64|| (0 otherwise); first = 1 records ||b64||.
+// binary64 residual: r64 = b64 - A64 x64 with per-column norms; scale = 1/||r64|| for
+// columns with ||r64|| > rtol ||b64|| (0 = converged); first = 1 records ||b64||.
 struct RefineState {
   double *obb, *orr, *scale;  // n_sd x kp
   double* part;               // n_tiles x kp
@@ -108,13 +109,19 @@ struct RefineState {
 void launch_residual64(const DTiles& tiles, const EllView<double>& A, const double* b64,
                        const double* x64, double* r64, int kp, int nc, double rtol2,
                        int first, const RefineState& s, cudaStream_t st);
-template <typename T>
-void launch_cast_scale(const DTiles& tiles, const double* r64, T* rT, int kp,
-                       const RefineState& s, cudaStream_t st);
-template <typename T>
-void launch_accumulate(const DTiles& tiles, const T* xT, double* x64, int kp,
-                       const RefineState& s, cudaStream_t st);
 void launch_zero_rows(const DTiles& tiles, double* x, int kp, cudaStream_t st);
+// residual replacement of the CG recursion: rT = (T) r64, rz recomputed, done flags from
+// the binary64 convergence test of launch_residual64 (scale == 0 means converged);
+// reopened columns restart with pT = D^{-1} rT
+template <typename T>
+void launch_cg_replace(const DTiles& tiles, const double* r64, T* rT, T* pT, const T* dinv,
+                       int kp, const CgState& s, const RefineState& rs, cudaStream_t st);
+// x64 += xT, xT = 0
+template <typename T>
+void launch_accum_reset(const DTiles& tiles, T* xT, double* x64, int kp, cudaStream_t st);
+// dst = (T) src on the rows of tiles
+template <typename T>
+void launch_cast(const DTiles& tiles, const double* src, T* dst, int kp, cudaStream_t st);
 
 // ---------------- dense per-subdomain kernels (mor_dense.cu) ----------------
 // G[sd] = X^T Y over the rows of tiles: nx x ny with row stride ldg and subdomain

@@ -8,6 +8,7 @@
 // last tile of a subdomain to finish (atomic ticket) reduces them in tile order, so the
 // reductions are deterministic and need no extra launch.
 #include "mor_kernels.h"
+#include "mor_plan.h"
 
 namespace mor {
 namespace {
@@ -41,27 +42,37 @@ __device__ __forceinline__ Geo geo() {
   return g;
 }
 
-// shared memory layout: red[nth * N] of T, then scratch[nth] doubles, then sums[2*kp]
+// shared memory layout: red[nth * N] of T, scratch[nth] doubles, sums[2*kp] doubles,
+// then the staged sliced-ELL tile: scol[kTileRows * W] int32, sval[kTileRows * W] T
 template <typename T>
 struct Smem {
   T* red;
   double* scratch;
   double* sums;
+  int32_t* scol;
+  T* sval;
 };
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 template <typename T>
-__device__ __forceinline__ Smem<T> smem_layout(const Geo& g, int kp) {
+__device__ __forceinline__ Smem<T> smem_layout(const Geo& g, int kp, int W) {
   extern __shared__ __align__(16) unsigned char raw[];
   Smem<T> s;
-  s.red = reinterpret_cast<T*>(raw);
-  s.scratch = reinterpret_cast<double*>(raw + ((sizeof(T) * 16 / sizeof(T) * g.nth + 15) & ~15));
+  size_t o = 0;
+  s.red = reinterpret_cast<T*>(raw + o);
+  o += align16(16 * (size_t)g.nth);
+  s.scratch = reinterpret_cast<double*>(raw + o);
   s.sums = s.scratch + g.nth;
-  (void)kp;
+  o += align16(sizeof(double) * ((size_t)g.nth + 2 * kp));
+  s.scol = reinterpret_cast<int32_t*>(raw + o);
+  o += align16(sizeof(int32_t) * (size_t)kTileRows * W);
+  s.sval = reinterpret_cast<T*>(raw + o);
   return s;
 }
 template <typename T>
-size_t smem_bytes(int nch, int rb, int kp) {
-  int nth = nch * rb;
-  return ((16 * (size_t)nth + 15) & ~(size_t)15) + sizeof(double) * (nth + 2 * kp);
+size_t smem_bytes(int nch, int rb, int kp, int W) {
+  size_t nth = (size_t)nch * rb;
+  return align16(16 * nth) + align16(sizeof(double) * (nth + 2 * kp)) +
+         align16(sizeof(int32_t) * (size_t)kTileRows * W) + sizeof(T) * (size_t)kTileRows * W;
 }
 
 // column sums over ty of per-thread N-wide accumulators -> out[tx*N + e] (double)
@@ -129,37 +140,172 @@ __device__ __forceinline__ void count_active(const Geo& g, const int* done, int 
   if (g.tid == 0) active[sd] = cnt;
 }
 
+// ---------------------------------------------------------------------------------
+// Sliced-ELL products on a row tile.  The tile's slots (column index and value) are
+// first staged in shared memory with coalesced loads (consecutive threads take
+// consecutive rows of one slot), which takes the index load off the critical path of
+// the gathers.  Thread (tx, ty) then computes the 16-byte column chunk tx of rows
+// ty, ty + RB, ...: eight slots are gathered (predicated, independent loads) before
+// their multiply-adds.  k_spmm: Y = A X.  k_cg_spmm_pq: q = A p with the column sums
+// of p.q.  k_residual64: r = b - A x with the column sums of r.r.
 template <typename T>
-__device__ __forceinline__ Pack<T> spmm_row(int64_t row, int tx, const EllView<T>& A,
-                                            const T* __restrict__ X, int kp) {
+__device__ __forceinline__ void stage_tile(const Geo& g, int r0, int nrows,
+                                           const EllView<T>& A, int32_t* scol, T* sval) {
+  const int W = A.W;
+  const bool full = nrows == kTileRows;  // full tiles: slot and row by shifts
+  for (int idx = g.tid; idx < nrows * W; idx += g.nth) {
+    int j, rr;
+    if (full) {
+      j = idx / kTileRows;  // kTileRows is a power of two: compiles to a shift
+      rr = idx & (kTileRows - 1);
+    } else {
+      j = idx / nrows;
+      rr = idx - j * nrows;
+    }
+    int64_t r = (int64_t)r0 + rr;
+    int32_t c = -1;
+    T v = T(0);
+    if (j < A.width[r >> 5]) {
+      int64_t at = ell_at(r, j, W);
+      c = A.col[at];
+      v = A.val[at];
+    }
+    scol[rr * W + j] = c;
+    sval[rr * W + j] = v;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ Pack<T> spmm_row(int rr, int w, int W, int tx, const int32_t* scol,
+                                            const T* sval, const T* __restrict__ X, int kp) {
   constexpr int N = Pack<T>::N;
+  constexpr int U = 8;
   Pack<T> acc;
 #pragma unroll
   for (int e = 0; e < N; ++e) acc.v[e] = T(0);
-  int w = A.width[row >> 5];
-#pragma unroll 4
-  for (int j = 0; j < w; ++j) {
-    int64_t at = ell_at(row, j, A.W);
-    int32_t c = A.col[at];
-    if (c < 0) continue;
-    T a = A.val[at];
-    Pack<T> x = ld(X + (int64_t)c * kp + tx * N);
+  const int32_t* cr = scol + rr * W;
+  const T* vr = sval + rr * W;
+  for (int j0 = 0; j0 < w; j0 += U) {
+    Pack<T> xv[U];
+    T av[U];
 #pragma unroll
-    for (int e = 0; e < N; ++e) acc.v[e] += a * x.v[e];
+    for (int u = 0; u < U; ++u) {
+      int j = j0 + u;
+      int32_t c = (j < w) ? cr[j] : -1;
+      av[u] = (j < w) ? vr[j] : T(0);
+      if (c >= 0) {
+        xv[u] = ld(X + (int64_t)c * kp + tx * N);
+      } else {
+#pragma unroll
+        for (int e = 0; e < N; ++e) xv[u].v[e] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < N; ++e) acc.v[e] += av[u] * xv[u].v[e];
   }
   return acc;
 }
 
-// ---------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_spmm(DTiles tl, EllView<T> A, const T* __restrict__ X, T* __restrict__ Y,
                        int kp) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
-  int tile = blockIdx.x;
-  int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  for (int64_t row = r0 + g.ty; row < r1; row += g.rb)
-    st(Y + row * kp + g.tx * N, spmm_row(row, g.tx, A, X, kp));
+  Smem<T> sm = smem_layout<T>(g, kp, A.W);
+  const int tile = blockIdx.x;
+  const int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
+  __syncthreads();
+  for (int rr = g.ty; rr < r1 - r0; rr += g.rb) {
+    int64_t row = r0 + rr;
+    st(Y + row * kp + g.tx * N,
+       spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, X, kp));
+  }
+}
+
+template <typename T>
+__global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
+                             T* __restrict__ q, int kp, CgState s) {
+  constexpr int N = Pack<T>::N;
+  Geo g = geo();
+  Smem<T> sm = smem_layout<T>(g, kp, A.W);
+  const int tile = blockIdx.x, sd = tl.sd[tile];
+  const int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
+  __syncthreads();
+  T acc[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) acc[e] = T(0);
+  for (int rr = g.ty; rr < r1 - r0; rr += g.rb) {
+    int64_t row = r0 + rr;
+    Pack<T> qv = spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, p, kp);
+    int64_t o = row * kp + g.tx * N;
+    st(q + o, qv);
+    Pack<T> pv = ld(p + o);
+#pragma unroll
+    for (int e = 0; e < N; ++e) acc[e] += pv.v[e] * qv.v[e];
+  }
+  block_colsum<T, N>(g, acc, sm.red, s.part1 + (int64_t)tile * kp);
+  const int lo = tl.lo[sd], hi = tl.hi[sd];
+  if (!last_block(g, s.counter, sd, hi - lo)) return;
+  sd_colsums(g, s.part1, kp, lo, hi, sm.scratch, sm.sums);
+  for (int c = g.tid; c < kp; c += g.nth) {
+    int i = sd * kp + c;
+    double a = 0.0;
+    if (!s.done[i]) {
+      double pq = sm.sums[c];
+      if (pq > 0.0)
+        a = s.rz[i] / pq;
+      else
+        s.done[i] = 1;  // breakdown (p = 0 or indefinite): stop this column
+    }
+    s.alpha[i] = a;
+  }
+}
+
+__global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restrict__ b,
+                             const double* __restrict__ x, double* __restrict__ r, int kp,
+                             int nc, double rtol2, int first, RefineState s) {
+  constexpr int N = 2;
+  Geo g = geo();
+  Smem<double> sm = smem_layout<double>(g, kp, A.W);
+  const int tile = blockIdx.x, sd = tl.sd[tile];
+  const int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
+  __syncthreads();
+  double acc[N] = {0.0, 0.0};
+  for (int rr = g.ty; rr < r1 - r0; rr += g.rb) {
+    int64_t row = r0 + rr;
+    Pack<double> ax = spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, x, kp);
+    int64_t o = row * kp + g.tx * N;
+    Pack<double> bv = ld(b + o), rv;
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      rv.v[e] = bv.v[e] - ax.v[e];
+      acc[e] += rv.v[e] * rv.v[e];
+    }
+    st(r + o, rv);
+  }
+  block_colsum<double, N>(g, acc, sm.red, s.part + (int64_t)tile * kp);
+  const int lo = tl.lo[sd], hi = tl.hi[sd];
+  if (!last_block(g, s.counter, sd, hi - lo)) return;
+  sd_colsums(g, s.part, kp, lo, hi, sm.scratch, sm.sums);
+  __shared__ int cnt;
+  if (g.tid == 0) cnt = 0;
+  __syncthreads();
+  for (int c = g.tid; c < kp; c += g.nth) {
+    int i = sd * kp + c;
+    double rr = sm.sums[c];
+    if (first) s.obb[i] = rr;
+    s.orr[i] = rr;
+    bool done = (c >= nc) || !(s.obb[i] > 0.0) || rr <= rtol2 * s.obb[i];
+    s.scale[i] = done ? 0.0 : 1.0 / sqrt(rr);
+    if (!done) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (g.tid == 0) s.active[sd] = cnt;
 }
 
 template <typename T>
@@ -167,7 +313,7 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r, T* p,
                           const T* __restrict__ dinv, int kp, int nc, CgState s) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
-  Smem<T> sm = smem_layout<T>(g, kp);
+  Smem<T> sm = smem_layout<T>(g, kp, 0);
   int tile = blockIdx.x, sd = tl.sd[tile];
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
   T arz[N], arr[N];
@@ -202,6 +348,7 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r, T* p,
     double bb = sm.sums[kp + c];
     s.rz[i] = sm.sums[c];
     s.bb[i] = bb;
+    s.rr[i] = bb;
     s.done[i] = (c >= nc || !(bb > 0.0)) ? 1 : 0;
     s.alpha[i] = 0.0;
     s.beta[i] = 0.0;
@@ -211,42 +358,6 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r, T* p,
   count_active(g, s.done, sd, kp, s.active);
 }
 
-template <typename T>
-__global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
-                             T* __restrict__ q, int kp, CgState s) {
-  constexpr int N = Pack<T>::N;
-  Geo g = geo();
-  Smem<T> sm = smem_layout<T>(g, kp);
-  int tile = blockIdx.x, sd = tl.sd[tile];
-  int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  T acc[N];
-#pragma unroll
-  for (int e = 0; e < N; ++e) acc[e] = T(0);
-  for (int64_t row = r0 + g.ty; row < r1; row += g.rb) {
-    Pack<T> qv = spmm_row(row, g.tx, A, p, kp);
-    int64_t o = row * kp + g.tx * N;
-    st(q + o, qv);
-    Pack<T> pv = ld(p + o);
-#pragma unroll
-    for (int e = 0; e < N; ++e) acc[e] += pv.v[e] * qv.v[e];
-  }
-  block_colsum<T, N>(g, acc, sm.red, s.part1 + (int64_t)tile * kp);
-  int lo = tl.lo[sd], hi = tl.hi[sd];
-  if (!last_block(g, s.counter, sd, hi - lo)) return;
-  sd_colsums(g, s.part1, kp, lo, hi, sm.scratch, sm.sums);
-  for (int c = g.tid; c < kp; c += g.nth) {
-    int i = sd * kp + c;
-    double a = 0.0;
-    if (!s.done[i]) {
-      double pq = sm.sums[c];
-      if (pq > 0.0)
-        a = s.rz[i] / pq;
-      else
-        s.done[i] = 1;  // breakdown (p = 0 or indefinite): stop this column
-    }
-    s.alpha[i] = a;
-  }
-}
 
 template <typename T>
 __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
@@ -254,7 +365,7 @@ __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
                                double tol2, CgState s) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
-  Smem<T> sm = smem_layout<T>(g, kp);
+  Smem<T> sm = smem_layout<T>(g, kp, 0);
   int tile = blockIdx.x, sd = tl.sd[tile];
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
   T al[N];
@@ -287,6 +398,7 @@ __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
   for (int c = g.tid; c < kp; c += g.nth) {
     int i = sd * kp + c;
     double be = 0.0;
+    s.rr[i] = sm.sums[c];
     if (!s.done[i]) {
       double rr = sm.sums[c], rzn = sm.sums[kp + c];
       if (rr <= tol2 * s.bb[i] || !(s.rz[i] > 0.0)) {
@@ -334,69 +446,6 @@ __global__ void k_count_active(int n_sd, const int* active, int* out) {
   if (threadIdx.x == 0) *out = tot;
 }
 
-__global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restrict__ b,
-                             const double* __restrict__ x, double* __restrict__ r, int kp,
-                             int nc, double rtol2, int first, RefineState s) {
-  constexpr int N = 2;
-  Geo g = geo();
-  Smem<double> sm = smem_layout<double>(g, kp);
-  int tile = blockIdx.x, sd = tl.sd[tile];
-  int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  double acc[N] = {0.0, 0.0};
-  for (int64_t row = r0 + g.ty; row < r1; row += g.rb) {
-    Pack<double> ax = spmm_row(row, g.tx, A, x, kp);
-    int64_t o = row * kp + g.tx * N;
-    Pack<double> bv = ld(b + o), rv;
-#pragma unroll
-    for (int e = 0; e < N; ++e) {
-      rv.v[e] = bv.v[e] - ax.v[e];
-      acc[e] += rv.v[e] * rv.v[e];
-    }
-    st(r + o, rv);
-  }
-  block_colsum<double, N>(g, acc, sm.red, s.part + (int64_t)tile * kp);
-  int lo = tl.lo[sd], hi = tl.hi[sd];
-  if (!last_block(g, s.counter, sd, hi - lo)) return;
-  sd_colsums(g, s.part, kp, lo, hi, sm.scratch, sm.sums);
-  __shared__ int cnt;
-  if (g.tid == 0) cnt = 0;
-  __syncthreads();
-  for (int c = g.tid; c < kp; c += g.nth) {
-    int i = sd * kp + c;
-    double rr = sm.sums[c];
-    if (first) s.obb[i] = rr;
-    s.orr[i] = rr;
-    bool done = (c >= nc) || !(s.obb[i] > 0.0) || rr <= rtol2 * s.obb[i];
-    s.scale[i] = done ? 0.0 : 1.0 / sqrt(rr);
-    if (!done) atomicAdd(&cnt, 1);
-  }
-  __syncthreads();
-  if (g.tid == 0) s.active[sd] = cnt;
-}
-
-template <typename T>
-__global__ void k_cast_scale(DTiles tl, const double* __restrict__ r64, T* __restrict__ rT,
-                             int kp, RefineState s) {
-  Geo g = geo();
-  int tile = blockIdx.x, sd = tl.sd[tile];
-  int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  for (int64_t row = r0 + g.ty; row < r1; row += g.rb)
-    for (int c = g.tx; c < kp; c += g.nch)
-      rT[row * kp + c] = (T)(r64[row * kp + c] * s.scale[sd * kp + c]);
-}
-
-template <typename T>
-__global__ void k_accumulate(DTiles tl, const T* __restrict__ xT, double* __restrict__ x64,
-                             int kp, RefineState s) {
-  Geo g = geo();
-  int tile = blockIdx.x, sd = tl.sd[tile];
-  int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  for (int64_t row = r0 + g.ty; row < r1; row += g.rb)
-    for (int c = g.tx; c < kp; c += g.nch) {
-      double sc = s.scale[sd * kp + c];
-      if (sc != 0.0) x64[row * kp + c] += (double)xT[row * kp + c] / sc;
-    }
-}
 
 __global__ void k_zero_rows(DTiles tl, double* x, int kp) {
   Geo g = geo();
@@ -404,6 +453,84 @@ __global__ void k_zero_rows(DTiles tl, double* x, int kp) {
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
   for (int64_t row = r0 + g.ty; row < r1; row += g.rb)
     for (int c = g.tx; c < kp; c += g.nch) x[row * kp + c] = 0.0;
+}
+
+// residual replacement: rT = (T) r64 (the true residual), rz recomputed from it, and
+// each column's done flag taken from the binary64 convergence test (scale == 0)
+// Columns the recursion had declared converged but the binary64 test reopens, and
+// columns whose true residual exceeds 1.5x the recursive one, restart from
+// p = D^{-1} r: their stored direction belongs to a much smaller residual.
+template <typename T>
+__global__ void k_cg_replace(DTiles tl, const double* __restrict__ r64, T* __restrict__ rT,
+                             T* __restrict__ pT, const T* __restrict__ dinv, int kp, CgState s,
+                             RefineState rs) {
+  constexpr int N = Pack<T>::N;
+  Geo g = geo();
+  Smem<T> sm = smem_layout<T>(g, kp, 0);
+  int tile = blockIdx.x, sd = tl.sd[tile];
+  int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  bool restart[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) {
+    int i = sd * kp + g.tx * N + e;
+    // reopened, or the recursion drifted from the true residual (a stale direction
+    // would make the next step length meaningless)
+    restart[e] = rs.scale[i] != 0.0 && (s.done[i] || rs.orr[i] > 2.25 * s.rr[i]);
+  }
+  T arz[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) arz[e] = T(0);
+  for (int64_t row = r0 + g.ty; row < r1; row += g.rb) {
+    int64_t o = row * kp + g.tx * N;
+    Pack<T> rv, pv = ld(pT + o);
+    T d = dinv[row];
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      rv.v[e] = (T)r64[o + e];
+      arz[e] += rv.v[e] * (d * rv.v[e]);
+      if (restart[e]) pv.v[e] = d * rv.v[e];
+    }
+    st(rT + o, rv);
+    st(pT + o, pv);
+  }
+  block_colsum<T, N>(g, arz, sm.red, s.part1 + (int64_t)tile * kp);
+  int lo = tl.lo[sd], hi = tl.hi[sd];
+  if (!last_block(g, s.counter, sd, hi - lo)) return;
+  sd_colsums(g, s.part1, kp, lo, hi, sm.scratch, sm.sums);
+  for (int c = g.tid; c < kp; c += g.nth) {
+    int i = sd * kp + c;
+    s.rz[i] = sm.sums[c];
+    s.bb[i] = rs.obb[i];
+    s.done[i] = (rs.scale[i] == 0.0) ? 1 : 0;
+    s.alpha[i] = 0.0;
+    s.beta[i] = 0.0;
+  }
+  __syncthreads();
+  count_active(g, s.done, sd, kp, s.active);
+}
+
+// x64 += xT; xT = 0
+template <typename T>
+__global__ void k_accum_reset(DTiles tl, T* __restrict__ xT, double* __restrict__ x64, int kp) {
+  Geo g = geo();
+  int tile = blockIdx.x;
+  int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  for (int64_t row = r0 + g.ty; row < r1; row += g.rb)
+    for (int c = g.tx; c < kp; c += g.nch) {
+      int64_t o = row * kp + c;
+      x64[o] += (double)xT[o];
+      xT[o] = T(0);
+    }
+}
+
+// rT = (T) src
+template <typename T>
+__global__ void k_cast(DTiles tl, const double* __restrict__ src, T* __restrict__ dst, int kp) {
+  Geo g = geo();
+  int tile = blockIdx.x;
+  int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  for (int64_t row = r0 + g.ty; row < r1; row += g.rb)
+    for (int c = g.tx; c < kp; c += g.nch) dst[row * kp + c] = (T)src[row * kp + c];
 }
 
 template <typename T>
@@ -417,11 +544,22 @@ dim3 block_of(int kp) {
 }  // namespace
 
 template <typename T>
+void set_smem_attr(const void* fn) {
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+}
+
+template <typename T>
 void launch_spmm(const DTiles& tiles, const EllView<T>& A, const T* X, T* Y, int kp,
                  cudaStream_t st) {
   if (tiles.n <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    set_smem_attr<T>((const void*)k_spmm<T>);
+    attr = true;
+  }
+  dim3 bl = block_of<T>(kp);
   count_launch();
-  k_spmm<T><<<tiles.n, block_of<T>(kp), 0, st>>>(tiles, A, X, Y, kp);
+  k_spmm<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, A.W), st>>>(tiles, A, X, Y, kp);
 }
 
 template <typename T>
@@ -430,8 +568,8 @@ void launch_cg_init(const DTiles& tiles, const T* b, T* x, T* r, T* p, const T* 
   if (tiles.n <= 0) return;
   dim3 bl = block_of<T>(kp);
   count_launch();
-  k_cg_init<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp), st>>>(tiles, b, x, r, p, dinv,
-                                                                   kp, nc, s);
+  k_cg_init<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, b, x, r, p, dinv,
+                                                                      kp, nc, s);
 }
 
 template <typename T>
@@ -439,13 +577,19 @@ void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, 
                     const T* dinv, int kp, double tol2, const CgState& s, cudaStream_t st,
                     const cudaEvent_t* ev) {
   if (tiles.n <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T>);
+    attr = true;
+  }
   dim3 bl = block_of<T>(kp);
-  size_t sb = smem_bytes<T>(bl.x, bl.y, kp);
   count_launch(3);
   if (ev) cudaEventRecord(ev[0], st);
-  k_cg_spmm_pq<T><<<tiles.n, bl, sb, st>>>(tiles, A, p, q, kp, s);
+  k_cg_spmm_pq<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, A.W), st>>>(tiles, A, p, q, kp,
+                                                                           s);
   if (ev) cudaEventRecord(ev[1], st);
-  k_cg_update_xr<T><<<tiles.n, bl, sb, st>>>(tiles, x, r, p, q, dinv, kp, tol2, s);
+  k_cg_update_xr<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, x, r, p, q,
+                                                                           dinv, kp, tol2, s);
   if (ev) cudaEventRecord(ev[2], st);
   k_cg_update_p<T><<<tiles.n, bl, 0, st>>>(tiles, r, p, dinv, kp, s);
   if (ev) cudaEventRecord(ev[3], st);
@@ -460,27 +604,51 @@ void launch_residual64(const DTiles& tiles, const EllView<double>& A, const doub
                        const double* x64, double* r64, int kp, int nc, double rtol2,
                        int first, const RefineState& s, cudaStream_t st) {
   if (tiles.n <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    set_smem_attr<double>((const void*)k_residual64);
+    attr = true;
+  }
   dim3 bl = block_of<double>(kp);
   count_launch();
-  k_residual64<<<tiles.n, bl, smem_bytes<double>(bl.x, bl.y, kp), st>>>(
+  k_residual64<<<tiles.n, bl, smem_bytes<double>(bl.x, bl.y, kp, A.W), st>>>(
       tiles, A, b64, x64, r64, kp, nc, rtol2, first, s);
 }
 
 template <typename T>
-void launch_cast_scale(const DTiles& tiles, const double* r64, T* rT, int kp,
-                       const RefineState& s, cudaStream_t st) {
+void launch_cg_replace(const DTiles& tiles, const double* r64, T* rT, T* pT, const T* dinv,
+                       int kp, const CgState& s, const RefineState& rs, cudaStream_t st) {
   if (tiles.n <= 0) return;
+  dim3 bl = block_of<T>(kp);
   count_launch();
-  k_cast_scale<T><<<tiles.n, dim3(32, 8), 0, st>>>(tiles, r64, rT, kp, s);
+  k_cg_replace<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, r64, rT, pT,
+                                                                         dinv, kp, s, rs);
 }
 
 template <typename T>
-void launch_accumulate(const DTiles& tiles, const T* xT, double* x64, int kp,
-                       const RefineState& s, cudaStream_t st) {
+void launch_accum_reset(const DTiles& tiles, T* xT, double* x64, int kp, cudaStream_t st) {
   if (tiles.n <= 0) return;
   count_launch();
-  k_accumulate<T><<<tiles.n, dim3(32, 8), 0, st>>>(tiles, xT, x64, kp, s);
+  k_accum_reset<T><<<tiles.n, dim3(32, 8), 0, st>>>(tiles, xT, x64, kp);
 }
+
+template <typename T>
+void launch_cast(const DTiles& tiles, const double* src, T* dst, int kp, cudaStream_t st) {
+  if (tiles.n <= 0) return;
+  count_launch();
+  k_cast<T><<<tiles.n, dim3(32, 8), 0, st>>>(tiles, src, dst, kp);
+}
+
+template void launch_cg_replace<float>(const DTiles&, const double*, float*, float*,
+                                       const float*, int, const CgState&, const RefineState&,
+                                       cudaStream_t);
+template void launch_cg_replace<double>(const DTiles&, const double*, double*, double*,
+                                        const double*, int, const CgState&, const RefineState&,
+                                        cudaStream_t);
+template void launch_accum_reset<float>(const DTiles&, float*, double*, int, cudaStream_t);
+template void launch_accum_reset<double>(const DTiles&, double*, double*, int, cudaStream_t);
+template void launch_cast<float>(const DTiles&, const double*, float*, int, cudaStream_t);
+template void launch_cast<double>(const DTiles&, const double*, double*, int, cudaStream_t);
 
 void launch_zero_rows(const DTiles& tiles, double* x, int kp, cudaStream_t st) {
   if (tiles.n <= 0) return;
@@ -502,13 +670,4 @@ template void launch_cg_step<float>(const DTiles&, const EllView<float>&, float*
 template void launch_cg_step<double>(const DTiles&, const EllView<double>&, double*, double*,
                                      double*, double*, const double*, int, double,
                                      const CgState&, cudaStream_t, const cudaEvent_t*);
-template void launch_cast_scale<float>(const DTiles&, const double*, float*, int,
-                                       const RefineState&, cudaStream_t);
-template void launch_cast_scale<double>(const DTiles&, const double*, double*, int,
-                                        const RefineState&, cudaStream_t);
-template void launch_accumulate<float>(const DTiles&, const float*, double*, int,
-                                       const RefineState&, cudaStream_t);
-template void launch_accumulate<double>(const DTiles&, const double*, double*, int,
-                                        const RefineState&, cudaStream_t);
-
 }  // namespace mor

@@ -36,7 +36,7 @@ class _MeshC(ctypes.Structure):
 class BasisOpts(ctypes.Structure):
     _fields_ = [("rank", _i32), ("oversample", _i32), ("seed", ctypes.c_uint64),
                 ("precision", _i32), ("sketch", _i32), ("cg_rtol", _dbl),
-                ("inner_rtol", _dbl), ("max_iter", _i32), ("max_refine", _i32),
+                ("max_iter", _i32), ("replace_every", _i32),
                 ("sketch_rtol", _dbl), ("tau", _dbl), ("orth_tol", _dbl)]
 
 

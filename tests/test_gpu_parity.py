@@ -150,7 +150,7 @@ def test_mixed_precision_within_1e6_energy_error(mor, cube16, gpu16):
     mesh, kappa, owner, p, sd = cube16
     u_d = gpu16[4]
     opts = mor.basis_opts(rank=p["rank"], oversample=p["oversample"], seed=p["seed"],
-                          precision="mixed", cg_rtol=1e-9, inner_rtol=1e-4)
+                          precision="mixed", cg_rtol=1e-9)
     bm = mor.Bases(sd, opts)
     assert bm.converged
     rm = mor.Reduced(sd, bm)
