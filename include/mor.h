@@ -8,10 +8,10 @@
  *                                 Sec. 6 step 1, Sec. 7.1 "r-hops")
  *   step 2  mor_build_bases       optimal local bases (Sec. 4, Sec. 6 step 2 and
  *                                 "Randomized numerical linear algebra")
- *   step 3  mor_project           Q^T A Q by the interface-only product (Eq. (17), Sec. 6
+ *   step 3  mor_project           Q^T A Q by the interface-only product (Eq. (23), Sec. 6
  *                                 step 3), then mor_solve_reduced (diagonally
  *                                 preconditioned CG on the reduced system, Sec. 6 step 3)
- * plus mor_lift (u~ = sum_i S_i Q_i x_i, Eq. (10) with Def. 3.1) and mor_energy_norm.
+ * plus mor_lift (u~ = sum_i S_i Q_i x_i, Eq. (11) with Def. 3.1) and mor_energy_norm.
  *
  * Model problem: -div(k grad u) = 1 in Omega, u = 0 on the boundary, P1 tetrahedra
  * (Sec. 2; a per-element coefficient k as in Sec. 7.2).
@@ -116,12 +116,12 @@ typedef struct {
  * max_iter 20000, replace_every 40, sketch_rtol 0, tau 1e-12, orth_tol 1e-14). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 
-/* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (16)):
+/* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (24)):
  * assemble A_II, A_IB, H^+ on T_i^+ and H_i, A[P_i,P_i] on omega_i; solve
  * A_II u_0 = b_I; sketch W (k columns, field mode); X = C_i A_II^{-1} A_IB W;
  * orthonormalise X in the H_i inner product (R_i X^ = Qh); T = A_BI A_II^{-1} C_i^T H_i X^;
  * G_B = T^T S_B^{-1} T with S_B^{-1} T from a solve with H^+ (Lemma 4.1), which equals
- * B B^T for the matrix B of Eq. (16); eig(G_B) gives sigma_j^2 and the rotation of the
+ * B B^T for the matrix B of Eq. (24); eig(G_B) gives sigma_j^2 and the rotation of the
  * top `rank` directions; V = D_i [u_0, X^ U_m]; Q_i = V W Lambda^{-1/2} from
  * eig(V^T A[P_i,P_i] V) (so Q_i^T A_ii Q_i = I); b~_i = Q_i^T b[P_i].
  * Returns MOR_ERR_NOT_CONVERGED (with the bases still built) if a local solve stopped
@@ -135,7 +135,7 @@ int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* opts, void* 
 int mor_bases_info(const mor_bases* h, int32_t* kq, int32_t* k, int32_t* kept,
                    int64_t* total_kept);
 
-/* sigma[host, n_sub x k]: the singular values of B (Eq. (16)) per subdomain, descending. */
+/* sigma[host, n_sub x k]: the singular values of B (Eq. (24)) per subdomain, descending. */
 int mor_bases_sigma(const mor_bases* h, double* sigma);
 
 /* Q_i of subdomain `sub` into out[host, |owned| x kq] (row-major; rows = owned dofs in
@@ -150,7 +150,7 @@ int mor_bases_get_bt(const mor_bases* h, double* out);
  * replacements (sum), columns not converged, 0, 0}. */
 int mor_bases_stats(const mor_bases* h, int64_t* stats);
 
-/* Step 3a (Eq. (17), Sec. 6 step 3): K~ with identity diagonal blocks (from step 2) and
+/* Step 3a (Eq. (23), Sec. 6 step 3): K~ with identity diagonal blocks (from step 2) and
  * off-diagonal blocks K~_ij = Q_i^T A_0[P_i, P_j] Q_j, A_0 assembled on the interface
  * elements omega_0 only, iterating over neighbouring pairs. */
 int mor_project(const mor_subdomains* sd, const mor_bases* b, void* stream,

@@ -13,7 +13,7 @@ fem        P1 tetrahedral element matrices and sparse assembly (Sec. 2, Sec. 4)
 subdomains overlapping subdomains, r-hop extensions, index sets I, B (Sec. 3, 7.1)
 basis      per-subdomain optimal local basis, explicit and randomized (Sec. 4, Sec. 6)
 reduced    stitching, projection Q^T A Q (explicit and interface-only), reduced solve
-           (Eq. (10), Sec. 6 step 3)
+           (Eq. (11), Eq. (23), Sec. 6 step 3)
 pipeline   the whole path on one mesh
 
 Every function is pinned by ``tests/test_oracle_*.py`` against facts fixed by the

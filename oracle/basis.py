@@ -4,14 +4,14 @@ Steps, in the paper's order and notation:
   1. assemble on T_i^+ the stiffness A^+ with blocks A_II, A_IB (interior I, boundary
      B), the H1 inner-product matrix H^+ (Lemma 4.2), on omega_i the H1 matrix H_i, the
      load b_I, and on the owned nodes A[P_i, P_i] and b[P_i];
-  2. solve Prob. 4 (zero boundary): u_0 = A_II^{-1} b_I, q_0 = C_i u_0;
+  2. solve Prob. "aux1" (zero boundary, Eq. (7)): u_0 = A_II^{-1} b_I, q_0 = C_i u_0;
   3. weights: R_i = chol(H_i) (upper), R_BB = bottom-right block of chol(H^+) in [I; B]
      order (Lemma 4.1);
   4a. explicit (Eq. (14)): SVD of R_i Z_i R_BB^{-1}, Z_i = C_i A_II^{-1} A_IB;
   4b. randomized (Sec. 6, "Randomized numerical linear algebra"): sketch
       Qh Rh = R_i C_i A_II^{-1} A_IB W with W = R_BB^{-1} S_i, then the SVD of
       Qh^T R_i C_i A_II^{-1} A_IB R_BB^{-1} evaluated with two left solves (the
-      transposed form of Eq. (16)); basis R_i^{-1} Qh U_m;
+      transposed form of Eq. (24)); basis R_i^{-1} Qh U_m;
   5. basis V = D_i [q_0, R_i^{-1} U_m] (stitching restriction to the owned nodes,
      Def. 3.1), then the diagonal-block update: eig of K_i = V^T A[P_i,P_i] V,
      Q_i = V W Lambda^{-1/2} over eigenvalues > tau * max, so Q_i^T A_ii Q_i = I;

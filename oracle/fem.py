@@ -1,4 +1,4 @@
-"""P1 tetrahedral finite elements (Sec. 2, Prob. 2 "dweak"; Sec. 4 inner products).
+"""P1 tetrahedral finite elements (Sec. 2, Prob. "dweak"; Sec. 4 inner products).
 
 Element quantities for a tetrahedron T with vertices x_0..x_3:
   barycentric gradients  G = [grad lambda_a]: with J = [x_1-x_0, x_2-x_0, x_3-x_0],
@@ -6,7 +6,7 @@ Element quantities for a tetrahedron T with vertices x_0..x_3:
                          grad lambda_0 = -(sum of the other three);
   volume                 |T| = det(J) / 6;
   stiffness              K_T[a,b] = k_T |T| grad lambda_a . grad lambda_b
-                         (bilinear form of -div(k grad u); k = 1 is the paper's Eq. (1));
+                         (bilinear form of -div(k grad u); k = 1 is the paper's model problem, Eq. (1));
   mass                   M_T[a,b] = |T| (1 + delta_ab) / 20;
   H1 inner product       K_T(k = 1) + M_T  (the forms of Sec. 4 defining R_i and R_BB);
   load                   int_T f lambda_a; for f = 1 this is |T| / 4.
@@ -114,7 +114,7 @@ def free_map(dirichlet):
 
 
 def global_system(mesh, kappa, f=None):
-    """Global stiffness A and load b on the free DOFs (Prob. 2)."""
+    """Global stiffness A and load b on the free DOFs (Prob. "dweak")."""
     G, vol = tet_geometry(mesh.xyz, mesh.tets)
     fmap, free = free_map(mesh.dirichlet)
     A = assemble_matrix(mesh.tets, stiffness_elements(G, vol, kappa), fmap, len(free))

@@ -1,4 +1,4 @@
-"""Stitching, projection and the reduced solve (Eq. (10), Def. 3.1, Eq. (17) "qtaq",
+"""Stitching, projection and the reduced solve (Eq. (11), Def. 3.1, Eq. (23),
 Sec. 6 step 3).
 
   stitched basis  the global matrix Q whose column block i holds Q_i on the owned

@@ -662,7 +662,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
                     vS, kp, st);
   TRY(solve(S.tP_all, Hp, false, vS, vG, k, 0, rt_sketch));
 
-  // ---- forward solve A_II [X | u_0] = [A_IB W | b_I] (Prob. 4 and the lifting) ----
+  // ---- forward solve A_II [X | u_0] = [A_IB W | b_I] (Prob. "aux1", Eq. (7), and the lifting of Eq. (8)) ----
   launch_spmm<double>(S.tP_I, A_IB.e64(), vG, vF, kp, st);
   launch_set_col(S.tP_I, loadP, vF, kp, k, st);
   TRY(solve(S.tP_I, A_II, true, vF, vX, k + 1, 1, rt));
@@ -679,7 +679,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
     std::swap(Xw, Zw);
   }
 
-  // ---- adjoint: T = A_BI A_II^{-1} C_i^T H_i X^ (two left solves, Eq. (16)) ----
+  // ---- adjoint: T = A_BI A_II^{-1} C_i^T H_i X^ (two left solves, the transposed form of Eq. (24)) ----
   launch_spmm<double>(S.tW, Hi.e64(), Xw, Yw, kp, st);
   CK(cudaMemsetAsync(vF, 0, nP * kp * sizeof(double), st));
   launch_scatter_rows(nW, S.w2p, Yw, kp, vF, kp, kp, st);

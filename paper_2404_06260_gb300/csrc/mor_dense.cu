@@ -1,6 +1,6 @@
 // Small dense per-subdomain linear algebra of step 2 (Sec. 4, Sec. 6): tall-skinny
 // Grams X^T Y, the symmetric eigensolver used for the H_i-orthonormalisation, the
-// singular values of the projected operator (Eq. (16)) and the diagonal-block update,
+// singular values of the projected operator (Eq. (24)) and the diagonal-block update,
 // and the k x k right-multiplications that apply their results to row blocks.
 #include "mor_kernels.h"
 

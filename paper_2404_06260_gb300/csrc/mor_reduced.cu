@@ -1,4 +1,4 @@
-// Step 3 (Eq. (17), Sec. 6 step 3): the off-diagonal blocks of Q^T A Q from the
+// Step 3 (Eq. (23), Sec. 6 step 3): the off-diagonal blocks of Q^T A Q from the
 // interface couplings of neighbouring subdomains, the reduced CG solve (diagonal
 // preconditioner = identity because every diagonal block is I after the step-2
 // update), and the lift u~ = sum_i S_i Q_i x_i.

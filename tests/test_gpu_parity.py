@@ -161,7 +161,7 @@ def test_mixed_precision_within_1e6_energy_error(mor, cube16, gpu16):
 
 
 def test_full_rank_basis_reproduces_fe_solution(mor):
-    # Eq. (7): with every boundary direction kept, the stitched bases span the FE
+    # Eq. (9): with every boundary direction kept, the stitched bases span the FE
     # solution; two slabs of the 8^3 cube, |B| = 49 boundary nodes, rank 49
     import torch
     n = 8

@@ -41,7 +41,7 @@ def test_lemma42_trace_norm_is_min_extension_norm(cube16):
 
 def test_local_solution_splits_into_load_part_and_lifting(cube16):
     # Sec. 5.1: u|omega_i = u_{i,0}|omega_i + Z_i (u|boundary), with the lifting of
-    # Prob. 5 solving A_II u_I = -A_IB z (the paper's matrix Z_i drops that sign)
+    # Prob. "aux2" (Eq. (8)) solving A_II u_I = -A_IB z (the paper's matrix Z_i drops that sign)
     mesh, kappa, owner, p, subs = cube16
     A, b, fmap, free = fem.global_system(mesh, kappa)
     u = np.zeros(mesh.n_nodes)
@@ -56,7 +56,7 @@ def test_local_solution_splits_into_load_part_and_lifting(cube16):
 
 
 def test_weighted_norm_equals_operator_norm(cube16):
-    # Eq. (12): ||Z|| = sup ||Z beta||_{1,omega} / ||beta||_trace = ||R_i Z R_BB^{-1}||_2;
+    # Eq. (13): ||Z|| = sup ||Z beta||_{1,omega} / ||beta||_trace = ||R_i Z R_BB^{-1}||_2;
     # the sup is the top generalized eigenvalue of (Z^T H_i Z, S_B), S_B = Schur of H^+
     mesh, kappa, owner, p, subs = cube16
     s = subs[1]
@@ -74,7 +74,7 @@ def test_weighted_norm_equals_operator_norm(cube16):
 
 
 def test_randomized_with_full_sketch_equals_explicit_svd(cube16):
-    # with k >= M the sketch spans the whole range: the randomized SVD of Eq. (16)
+    # with k >= M the sketch spans the whole range: the randomized SVD of Eq. (24)
     # gives the singular values and top subspace of the explicit SVD (Eq. (14))
     mesh, kappa, owner, p, subs = cube16
     s = subs[2]

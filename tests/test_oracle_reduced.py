@@ -1,4 +1,4 @@
-"""Pins for the oracle's stitching, projection and reduced solve (Def. 3.1, Eq. (17),
+"""Pins for the oracle's stitching, projection and reduced solve (Def. 3.1, Eq. (23),
 Sec. 6 step 3, Sec. 7.1)."""
 import math
 
@@ -24,7 +24,7 @@ def cube16_run():
 
 def test_interface_projection_equals_explicit_qtaq(cube16_run):
     # Sec. 6 step 3: K~ built from step-2 diagonal blocks and A_0 on omega_0 equals
-    # Q^T A Q with the assembled global A (Eq. (17))
+    # Q^T A Q with the assembled global A (Eq. (23))
     mesh, kappa, owner, p, out = cube16_run
     A, b, _, _ = fem.global_system(mesh, kappa)
     K, bt = reduced.project_explicit(A, b, reduced.stitched_Q(mesh, out["bases"]))
@@ -58,7 +58,7 @@ def test_galerkin_energy_below_fe_energy_and_monotone_in_rank():
 
 @pytest.mark.parametrize("explicit", [True, False])
 def test_full_rank_basis_reproduces_fe_solution(explicit):
-    # Eq. (7): {u_{i,0}, Z_i phi_1..M} represents the local solution for any trace, so
+    # Eq. (9): {u_{i,0}, Z_i phi_1..M} represents the local solution for any trace, so
     # stitching the full bases reproduces the FE solution (Sec. 5.2 splitting)
     n = 12
     mesh = synth.kuhn_cube(n)
