@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cube64_p4")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run one mixed-precision build of the workload and exit (the "
+                         "command profiled by ncu)")
     return ap.parse_args()
 
 
@@ -345,10 +348,31 @@ def ours(args):
     return 0
 
 
+def profile_case(args):
+    import torch
+
+    import synth
+    from paper_2404_06260_gb300 import _build
+    _build.build()
+    from paper_2404_06260_gb300 import mor
+    mesh, kappa, owner, p = synth.workload(args.workload)
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, p["r_hops"])
+    opts = mor.basis_opts(rank=p["rank"], oversample=p["oversample"], seed=p["seed"],
+                          precision="mixed", cg_rtol=1e-9)
+    b = mor.Bases(sd, opts)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.workload, "basis_cols": int(b.total_kept),
+                      "iterations": b.stats()[:5].tolist()}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_case:
+        return profile_case(args)
     return ours(args)
 
 
