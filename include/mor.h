@@ -175,6 +175,36 @@ typedef struct {
 int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void* stream,
                       double* x_dev, mor_solve_info* info);
 
+/* mor_solve_reduced without any allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library allocate device memory, such as a
+ * host application whose device memory is owned by its own allocator or memory pool,
+ * or a time-critical loop that cannot afford cudaMalloc's implicit device-wide
+ * synchronization.  It runs the same CG iteration as mor_solve_reduced and makes no
+ * call to cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Inputs [device, caller-owned]: the block-sparse reduced matrix as in mor_project:
+ *   nbr_ptr_dev[n_sub + 1], nbr_sub_dev[], nbr_blk_dev[] list, per block row i, its
+ *   off-diagonal blocks (neighbour subdomain, block index); blocks_dev holds
+ *   kq x kq row-major blocks; the diagonal blocks are the identity and are not stored.
+ *   bt_dev[n_sub * kq] is the reduced load.
+ * Output [device, caller-owned]: x_dev[n_sub * kq].  info [host] may be NULL.
+ * Work space: a fixed device array inside the library (about 12.5 MB: the three CG
+ * vectors plus partial sums), held by every GPU that loads the library until the
+ * process exits.  Limits: n_sub * kq <= 524288 and n_sub <= 65536; larger systems are
+ * rejected with MOR_ERR_ARG and a message.
+ * The first call on a device looks up the array's device address with that device
+ * current and caches it; make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind; the call clears the
+ * state that must start at zero.  Calls whose GPU work overlaps (for example on two
+ * streams, or two host threads) race on the array: serialise them.
+ * Returns MOR_OK, MOR_ERR_NOT_CONVERGED (x holds the last iterate), MOR_ERR_ARG or
+ * MOR_ERR_CUDA. */
+int mor_solve_reduced_noalloc(int32_t n_sub, int32_t kq, const int32_t* nbr_ptr_dev,
+                              const int32_t* nbr_sub_dev, const int32_t* nbr_blk_dev,
+                              const double* blocks_dev, const double* bt_dev, double rtol,
+                              int32_t max_iter, void* stream, double* x_dev,
+                              mor_solve_info* info);
+
 /* u~ = sum_i S_i Q_i x_i on all nodes (zero on the Dirichlet boundary):
  * x_dev [device, dim], u_dev [device, n_nodes]. */
 int mor_lift(const mor_subdomains* sd, const mor_bases* b, const double* x_dev,

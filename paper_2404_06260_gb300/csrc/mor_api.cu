@@ -141,6 +141,9 @@ int round_up4(int x) { return (x + 3) & ~3; }
 
 }  // namespace
 
+// error reporting for the other translation units (same thread-local message)
+int mor::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 // ======================================================================================
 struct mor_subdomains_s {
   HostPlan hp;

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <string>
 
 #include "mor_dev.cuh"
 
@@ -13,6 +14,9 @@ namespace mor {
 // launches before enqueuing them)
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// record a failure for mor_last_error (thread-local) and return code
+int set_error(int code, const std::string& msg);
 
 // ---------------- assembly (mor_assembly.cu) ----------------
 // Row-gather P1 assembly (Sec. 2, Sec. 4): for every row the element contributions

@@ -67,6 +67,8 @@ _sig("mor_project", _i32, _P, _P, _P, ctypes.POINTER(_P))
 _sig("mor_reduced_info", _i32, _P, ctypes.POINTER(_i64), ctypes.POINTER(_i64))
 _sig("mor_reduced_dense", _i32, _P, _P)
 _sig("mor_solve_reduced", _i32, _P, _dbl, _i32, _P, _P, ctypes.POINTER(SolveInfo))
+_sig("mor_solve_reduced_noalloc", _i32, _i32, _i32, _P, _P, _P, _P, _P, _dbl, _i32, _P, _P,
+     ctypes.POINTER(SolveInfo))
 _sig("mor_lift", _i32, _P, _P, _P, _P, _P)
 _sig("mor_energy_norm", _i32, _P, _P, _P, ctypes.POINTER(_dbl), _P)
 _sig("mor_debug_sketch_rhs", _i32, _P, ctypes.POINTER(BasisOpts), _i32, _P, _P)
@@ -82,7 +84,8 @@ _sig("mor_last_error", ctypes.c_char_p)
 EXPORTED = ["mor_build_subdomains", "mor_subdomains_counts", "mor_subdomains_indices",
             "mor_basis_opts_default", "mor_build_bases", "mor_bases_info", "mor_bases_sigma",
             "mor_bases_get_Q", "mor_bases_get_bt", "mor_bases_stats", "mor_project",
-            "mor_reduced_info", "mor_reduced_dense", "mor_solve_reduced", "mor_lift",
+            "mor_reduced_info", "mor_reduced_dense", "mor_solve_reduced",
+            "mor_solve_reduced_noalloc", "mor_lift",
             "mor_energy_norm", "mor_debug_sketch_rhs", "mor_profile_enable",
             "mor_profile_reset", "mor_profile_query", "mor_kernel_launches", "mor_free_subdomains",
             "mor_free_bases", "mor_free_reduced", "mor_last_error"]
