@@ -74,13 +74,15 @@ typedef struct {
  * subdomain i: P_i = owned nodes; omega_i = elements touching P_i; the extension
  * T_i^+ = elements touching the r_hops-hop ball of P_i in the edge graph of the mesh;
  * I = free nodes of T_i^+ all of whose elements lie in T_i^+, B = its other free nodes.
- * r_hops >= 1.  The mesh's device arrays are referenced, not copied. */
+ * r_hops >= 1, or r_hops = -1 for a per-subdomain rule r_i = max(1, round(|P_i|^(1/3)/2))
+ * (about half the subdomain width, so the extension roughly doubles its diameter,
+ * Sec. 7.1).  The mesh's device arrays are referenced, not copied. */
 int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
                          void* stream, mor_subdomains** out);
 
-/* Sizes of step 1.  counts[host, n_sub x 6] receives per subdomain
- * {|I|, |B|, |omega dofs|, |owned dofs|, |T_i^+|, |omega_i elements|}; n_sub_out may
- * be NULL.  Pass counts = NULL to query n_sub only. */
+/* Sizes of step 1.  counts[host, n_sub x 7] receives per subdomain
+ * {|I|, |B|, |omega dofs|, |owned dofs|, |T_i^+|, |omega_i elements|, r_i}; n_sub_out
+ * may be NULL.  Pass counts = NULL to query n_sub only. */
 int mor_subdomains_counts(const mor_subdomains* h, int32_t* n_sub_out, int64_t* counts);
 
 /* Copy one index list of subdomain `sub` (global node ids, ascending) into out[host]:
@@ -94,6 +96,10 @@ int mor_subdomains_indices(const mor_subdomains* h, int32_t sub, int32_t which,
 typedef struct {
   int32_t rank;        /* m: singular vectors kept per subdomain (fixed-rank mode)      */
   int32_t oversample;  /* p: k = m + p sketch columns (Halko et al., App. B)           */
+  const int32_t* ranks; /* [host, n_sub] per-subdomain m_i replacing `rank` (may be NULL):
+                          subdomain i sketches k_i = m_i + p columns                    */
+  double eps;          /* > 0: tolerance mode (Eq. (15)): keep the sigma_j > eps among
+                          the k_i computed, instead of the first m_i                    */
   uint64_t seed;       /* Philox-4x32-10 key of the Gaussian draws                      */
   int32_t precision;   /* MOR_FP64 or MOR_MIXED                                         */
   int32_t sketch;      /* MOR_SKETCH_FIELD                                              */
@@ -103,6 +109,14 @@ typedef struct {
   int32_t replace_every; /* the CG residual is replaced by the binary64 residual
                           b - A x every replace_every iterations (rounded to a multiple
                           of 8) and whenever the recursion reports convergence         */
+  int32_t normwise;    /* 1: the lifting columns of a subdomain share one reference,
+                          the largest right-hand side of its block (the weighted SVD
+                          needs the block accurate normwise); 0: each column is
+                          measured against its own right-hand side.  The load column
+                          u_0 is always measured against its own.                       */
+  double drift_restart; /* at a replacement, a column whose true residual norm exceeds
+                          drift_restart x its recursive one restarts from p = D^{-1} r
+                          (its search direction no longer matches the residual)       */
   double sketch_rtol;  /* tolerance of the sketch solve W = ((H^+)^{-1} L xi)_B; W only
                           has to be a Gaussian-like test matrix, so it may be loose
                           (<= 0: use cg_rtol)                                           */
@@ -113,7 +127,8 @@ typedef struct {
 } mor_basis_opts;
 
 /* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
- * max_iter 20000, replace_every 40, sketch_rtol 0, tau 1e-12, orth_tol 1e-14). */
+ * max_iter 20000, replace_every 40, normwise 1, drift_restart 1.5, sketch_rtol 0,
+ * tau 1e-12, orth_tol 1e-14). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 
 /* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (24)):
@@ -129,13 +144,14 @@ int mor_basis_opts_default(mor_basis_opts* opts);
 int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* opts, void* stream,
                     mor_bases** out);
 
-/* Sizes of step 2: *kq = columns stored per subdomain (>= rank + 1, multiple of 4),
- * *k = sketch columns; kept[host, n_sub] = basis columns kept per subdomain (may be
- * NULL); *total_kept = sum of kept (may be NULL). */
+/* Sizes of step 2: *kq = columns stored per subdomain (>= max m_i + 1, multiple of 4),
+ * *k = the largest sketch width k_i; kept[host, n_sub] = basis columns kept per
+ * subdomain (may be NULL); *total_kept = sum of kept (may be NULL). */
 int mor_bases_info(const mor_bases* h, int32_t* kq, int32_t* k, int32_t* kept,
                    int64_t* total_kept);
 
-/* sigma[host, n_sub x k]: the singular values of B (Eq. (24)) per subdomain, descending. */
+/* sigma[host, n_sub x k]: the singular values of B (Eq. (24)) per subdomain, descending
+ * (zeros beyond k_i). */
 int mor_bases_sigma(const mor_bases* h, double* sigma);
 
 /* Q_i of subdomain `sub` into out[host, |owned| x kq] (row-major; rows = owned dofs in

@@ -16,9 +16,10 @@ def run(mesh, kappa, owner, rank, oversample, r_hops, seed, sketch="field",
         explicit=False, eps=None, tau=1e-12, f=None, keep_all=False, fe_solution=True,
         interface=True):
     subs = all_subdomains(mesh, owner, r_hops)
-    bases = [local_basis(mesh, kappa, s, rank, oversample, seed, sketch=sketch,
+    ranks = np.broadcast_to(np.asarray(rank), (len(subs),))   # per-subdomain m_i
+    bases = [local_basis(mesh, kappa, s, int(ranks[j]), oversample, seed, sketch=sketch,
                          explicit=explicit, eps=eps, tau=tau, f=f, keep_all=keep_all)
-             for s in subs]
+             for j, s in enumerate(subs)]
     out = dict(subs=subs, bases=bases)
     if interface:
         K, bt, pairs = project_interface(mesh, kappa, owner, bases)

@@ -27,6 +27,15 @@ def node_adjacency(tets, n_nodes):
     return A.tocsr()
 
 
+def hops_for(n_owned, r_hops):
+    """r_hops, or for r_hops = -1 about half the subdomain width:
+    max(1, round(n_owned^(1/3) / 2)) (halves round up), so the extension roughly
+    doubles the diameter (Sec. 7.1)."""
+    if r_hops > 0:
+        return r_hops
+    return max(1, int(np.floor(np.cbrt(float(n_owned)) / 2.0 + 0.5)))
+
+
 def subdomain_sets(mesh, owner, i, r_hops, adj=None):
     n = mesh.n_nodes
     tets = mesh.tets
@@ -34,7 +43,7 @@ def subdomain_sets(mesh, owner, i, r_hops, adj=None):
         adj = node_adjacency(tets, n)
     P = owner == i
     ball = P.copy()
-    for _ in range(r_hops):
+    for _ in range(hops_for(int(P.sum()), r_hops)):
         ball = ball | ((adj @ ball.astype(np.int8)) > 0)
     plus_t = np.flatnonzero(ball[tets].any(axis=1))
     omega_t = np.flatnonzero(P[tets].any(axis=1))

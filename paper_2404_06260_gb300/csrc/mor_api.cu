@@ -271,13 +271,14 @@ int mor_subdomains_counts(const mor_subdomains* h, int32_t* n_sub_out, int64_t* 
   if (counts)
     for (int i = 0; i < h->hp.n_sd; ++i) {
       const SubSets& s = h->hp.sets[i];
-      int64_t* c = counts + 6 * (int64_t)i;
+      int64_t* c = counts + 7 * (int64_t)i;
       c[0] = (int64_t)s.I.size();
       c[1] = (int64_t)s.B.size();
       c[2] = (int64_t)s.omega.size();
       c[3] = (int64_t)s.owned.size();
       c[4] = (int64_t)s.plus_tets.size();
       c[5] = (int64_t)s.omega_tets.size();
+      c[6] = (int64_t)h->hp.r_sd[i];
     }
   return MOR_OK;
 }
@@ -296,12 +297,16 @@ int mor_basis_opts_default(mor_basis_opts* o) {
   if (!o) return fail(MOR_ERR_ARG, "mor_basis_opts_default: null");
   o->rank = 8;
   o->oversample = 5;
+  o->ranks = nullptr;
+  o->eps = 0.0;
   o->seed = 0;
   o->precision = MOR_MIXED;
   o->sketch = MOR_SKETCH_FIELD;
   o->cg_rtol = 1e-9;
   o->max_iter = 20000;
   o->replace_every = 40;
+  o->normwise = 1;
+  o->drift_restart = 1.5;
   o->sketch_rtol = 0.0;
   o->tau = 1e-12;
   o->orth_tol = 1e-14;
@@ -355,6 +360,9 @@ struct Build {
   template <typename T>
   int solve(const DTiles& tl, const Mat& A, const T* dinvT, const double* b64, double* x64,
             int nc, int which, double rtol) {
+    // columns [0, ncn) share the block-normwise reference; the load column (forward
+    // solve, column k) keeps its own
+    const int ncn = o->normwise ? std::min(nc, k) : 0;
     EllView<T> AT;
     if constexpr (sizeof(T) == 4)
       AT = A.e32();
@@ -373,10 +381,10 @@ struct Build {
     // replace_every iterations and whenever the recursion reports convergence
     // (residual replacement keeps the search directions, so no Krylov restart)
     launch_zero_rows(tl, x64, kp, st);
-    launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, rtol2, 1, rs, st);
+    launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 1, rs, st);
     if (poll(rs.active) == 0) return MOR_OK;
     launch_cast<T>(tl, vR64, b, kp, st);
-    launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, cs, st);
+    launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, ncn, cs, st);
     const int check = 8;
     const int every = std::max(check, o->replace_every / check * check);
     int it = 0;
@@ -395,7 +403,7 @@ struct Build {
       int act = poll(cs.active);
       if (act == 0 || it % every == 0 || it >= o->max_iter) {
         launch_accum_reset<T>(tl, x, x64, kp, st);
-        launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, rtol2, 0, rs, st);
+        launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 0, rs, st);
         ++sweeps;
         int ract = poll(rs.active);
         if (debug) {
@@ -417,7 +425,7 @@ struct Build {
           not_conv += ract;
           break;
         }
-        launch_cg_replace<T>(tl, vR64, r, p, dinvT, kp, cs, rs, st);
+        launch_cg_replace<T>(tl, vR64, r, p, dinvT, kp, o->drift_restart, cs, rs, st);
       }
     }
     iters[which] += it;
@@ -470,17 +478,28 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   if (!sd || !opts || !out) return fail(MOR_ERR_ARG, "mor_build_bases: null argument");
   *out = nullptr;
   const mor_basis_opts& o = *opts;
-  if (o.rank < 1 || o.oversample < 0)
-    return fail(MOR_ERR_ARG, "mor_build_bases: rank >= 1 and oversample >= 0 required");
-  int k = o.rank + o.oversample;
-  int kp = round_up4(k + 1);
-  int kq = round_up4(o.rank + 1);
+  const int n_sd_h = sd->hp.n_sd;
+  std::vector<int32_t> h_rank(n_sd_h), h_k(n_sd_h);
+  for (int i = 0; i < n_sd_h; ++i) h_rank[i] = o.ranks ? o.ranks[i] : o.rank;
+  int m_max = 0;
+  for (int i = 0; i < n_sd_h; ++i) {
+    if (h_rank[i] < 1 || o.oversample < 0)
+      return fail(MOR_ERR_ARG, "mor_build_bases: ranks >= 1 and oversample >= 0 required");
+    h_k[i] = h_rank[i] + o.oversample;
+    m_max = std::max(m_max, h_rank[i]);
+  }
+  const int k = m_max + o.oversample;     // widest sketch; the load column sits at k
+  const int kp = round_up4(k + 1);
+  const bool tol_mode = o.eps > 0.0;
+  const int kq = round_up4((tol_mode ? k : m_max) + 1);
+  const int mcols = kq - 1 < (tol_mode ? k : m_max) ? kq - 1 : (tol_mode ? k : m_max);
   if (kp > 80 || kq > 80)
     return fail(MOR_ERR_ARG, "mor_build_bases: rank + oversample must be <= 79");
+  if (!(o.eps >= 0.0)) return fail(MOR_ERR_ARG, "mor_build_bases: eps must be >= 0");
   if (o.precision != MOR_FP64 && o.precision != MOR_MIXED)
     return fail(MOR_ERR_ARG, "mor_build_bases: unknown precision");
   if (o.sketch != MOR_SKETCH_FIELD) return fail(MOR_ERR_ARG, "mor_build_bases: unknown sketch");
-  if (!(o.cg_rtol > 0.0) || o.max_iter < 1 || o.replace_every < 1)
+  if (!(o.cg_rtol > 0.0) || o.max_iter < 1 || o.replace_every < 1 || !(o.drift_restart >= 1.0))
     return fail(MOR_ERR_ARG, "mor_build_bases: bad solver tolerances");
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -494,7 +513,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   B.k = k;
   B.kp = kp;
   B.kq = kq;
-  B.m = o.rank;
+  B.m = mcols;
   B.mixed = o.precision == MOR_MIXED;
   Allocs& M = B.mem;
   const int n_sd = hp.n_sd;
@@ -642,7 +661,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   Bo.k = k;
   Bo.kp = kp;
   Bo.kq = kq;
-  Bo.m = o.rank;
+  Bo.m = mcols;
   Bo.Ooff = hp.Ooff;
   TRY(Bo.mem.alloc(&Bo.Q, nO * kq, true, st));
   TRY(Bo.mem.alloc(&Bo.bt, (size_t)n_sd * kq, true, st));
@@ -661,8 +680,12 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   double* lrow;
   TRY(M.alloc(&lrow, nIncP * 4, false, st));
   launch_elem_lrow(nIncP, S.incP_tet, S.incP_code, S.xyz, S.tets, lrow, st);
+  int32_t *d_ksd, *d_msd, *d_msel;
+  TRY(M.upload(&d_ksd, h_k, st));
+  TRY(M.upload(&d_msd, h_rank, st));
+  TRY(M.alloc(&d_msel, n_sd, true, st));
   launch_sketch_rhs(B.mixed, 0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lrow, k, o.seed,
-                    vS, kp, st);
+                    vS, kp, st, d_ksd);
   TRY(solve(S.tP_all, Hp, false, vS, vG, k, 0, rt_sketch));
 
   // ---- forward solve A_II [X | u_0] = [A_IB W | b_I] (Prob. "aux1", Eq. (7), and the lifting of Eq. (8)) ----
@@ -695,17 +718,21 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   // eig(G_B) = sigma_j^2 (kept on the device as squares); the rotation of the top
   // `rank` directions gives the basis X^ U_m = R_i^{-1} Qh U_m
   launch_sym_eig(n_sd, G, kp, k, Bo.sigma, evecs, st);
-  launch_make_M(n_sd, 1, Bo.sigma, evecs, kp, k, 0.0, o.rank, Mm, kcnt, st);
-  launch_rowmul(S.tW, Xw, kp, k, Mm, kp, Zw, kp, o.rank, st);
+  // fixed rank: the first m_i directions; tolerance mode: sigma_j > eps (Eq. (15))
+  if (tol_mode)
+    launch_make_M(n_sd, 2, Bo.sigma, evecs, kp, k, o.eps * o.eps, mcols, Mm, d_msel, st, d_ksd);
+  else
+    launch_make_M(n_sd, 1, Bo.sigma, evecs, kp, k, 0.0, mcols, Mm, d_msel, st, d_msd);
+  launch_rowmul(S.tW, Xw, kp, k, Mm, kp, Zw, kp, mcols, st);
 
   // ---- V = D_i [u_0, X^ U_m], diagonal-block update Q_i = V W Lambda^{-1/2} ----
   launch_gather_rows(nO, S.o2w, u0w, 1, 0, V, kq, 0, 1, st);
-  launch_gather_rows(nO, S.o2w, Zw, kp, 0, V, kq, 1, o.rank, st);
+  launch_gather_rows(nO, S.o2w, Zw, kp, 0, V, kq, 1, mcols, st);
   launch_spmm<double>(S.tO, App.e64(), V, AV, kq, st);
-  launch_gram(S.tO, n_sd, V, kq, o.rank + 1, AV, kq, o.rank + 1, gpart, gcnt, G, kq, st);
-  launch_sym_eig(n_sd, G, kq, o.rank + 1, evals, evecs, st);
-  launch_make_M(n_sd, 0, evals, evecs, kq, o.rank + 1, o.tau, 0, Mm, Bo.kept, st);
-  launch_rowmul(S.tO, V, kq, o.rank + 1, Mm, kq, Bo.Q, kq, o.rank + 1, st);
+  launch_gram(S.tO, n_sd, V, kq, mcols + 1, AV, kq, mcols + 1, gpart, gcnt, G, kq, st);
+  launch_sym_eig(n_sd, G, kq, mcols + 1, evals, evecs, st);
+  launch_make_M(n_sd, 0, evals, evecs, kq, mcols + 1, o.tau, 0, Mm, Bo.kept, st);
+  launch_rowmul(S.tO, V, kq, mcols + 1, Mm, kq, Bo.Q, kq, mcols + 1, st);
   // b~_i = Q_i^T b[P_i]
   launch_gather_rows(nO, S.o2w, loadW, 1, 0, bP, 1, 0, 1, st);
   launch_gram(S.tO, n_sd, Bo.Q, kq, kq, bP, 1, 1, gpart, gcnt, Bo.bt, kq, st);
@@ -927,7 +954,7 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, i
   TRY(A.alloc(&res, (hp.nP) * (size_t)k, true, st));
   launch_elem_lrow(nInc, sd->incP_tet, sd->incP_code, sd->xyz, sd->tets, lrow, st);
   launch_sketch_rhs(opts->precision == MOR_MIXED, row0, n_rows, sd->p_sd, sd->incP_ptr,
-                    sd->incP_tet, sd->incP_code, lrow, k, opts->seed, res, k, st);
+                    sd->incP_tet, sd->incP_code, lrow, k, opts->seed, res, k, st, nullptr);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, res + row0 * k, n_rows * k * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

@@ -98,14 +98,17 @@ __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __rest
                              const int64_t* __restrict__ inc_ptr,
                              const int32_t* __restrict__ inc_tet,
                              const double* __restrict__ lrow, int k, uint64_t seed,
-                             double* __restrict__ out, int ld) {
+                             double* __restrict__ out, int ld,
+                             const int32_t* __restrict__ k_sd) {
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= n_rows) return;
   int64_t r = row0 + w;
   uint32_t sd = (uint32_t)row_sd[r];
   int64_t q0 = inc_ptr[r], q1 = inc_ptr[r + 1];
-  for (int j = lane; j < k; j += 32) {
+  const int kk = k_sd ? min(k, (int)k_sd[sd]) : k;
+  for (int j = lane + kk; j < k; j += 32) out[r * ld + j] = 0.0;
+  for (int j = lane; j < kk; j += 32) {
     double acc = 0.0;
     float accf = 0.0f;
     for (int64_t q = q0; q < q1; ++q) {
@@ -127,7 +130,7 @@ __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __rest
 void launch_sketch_rhs(bool fast, int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int64_t* inc_ptr, const int32_t* inc_tet,
                        const uint32_t* inc_code, const double* lrow, int k, uint64_t seed,
-                       double* out, int ld, cudaStream_t st) {
+                       double* out, int ld, cudaStream_t st, const int32_t* k_sd) {
   (void)inc_code;
   if (n_rows <= 0) return;
   int bs = 256;
@@ -135,10 +138,10 @@ void launch_sketch_rhs(bool fast, int64_t row0, int64_t n_rows, const int32_t* r
   count_launch();
   if (fast)
     k_sketch_rhs<true><<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, lrow, k,
-                                            seed, out, ld);
+                                            seed, out, ld, k_sd);
   else
     k_sketch_rhs<false><<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, lrow, k,
-                                             seed, out, ld);
+                                             seed, out, ld, k_sd);
 }
 
 // one thread per destination row; warps cover whole slices so the slice width is a

@@ -190,33 +190,27 @@ __global__ void k_sym_eig(const double* __restrict__ A, int ld, int n, double* e
 
 __global__ void k_make_M(int mode, const double* __restrict__ evals,
                          const double* __restrict__ evecs, int ld, int n, double rel, int keep,
-                         double* M, int* kept) {
+                         double* M, int* kept, const int32_t* __restrict__ keep_sd) {
   int sd = blockIdx.x;
   const double* ev = evals + (int64_t)sd * ld;
   const double* V = evecs + (int64_t)sd * ld * ld;
   double* Ms = M + (int64_t)sd * ld * ld;
   double l0 = ev[0];
+  const int kmax = keep_sd ? min(keep, (int)keep_sd[sd]) : keep;
+  auto take = [&](int j) -> bool {
+    if (mode == 0) return l0 > 0.0 && ev[j] > rel * l0;
+    if (mode == 1) return j < kmax;
+    return j < kmax && ev[j] > rel;
+  };
   for (int idx = threadIdx.x; idx < ld * ld; idx += blockDim.x) {
     int l = idx / ld, j = idx % ld;
     double val = 0.0;
-    if (l < n && j < n) {
-      if (mode == 0) {
-        double lj = ev[j];
-        if (l0 > 0.0 && lj > rel * l0) val = V[l * ld + j] / sqrt(lj);
-      } else if (j < keep) {
-        val = V[l * ld + j];
-      }
-    }
+    if (l < n && j < n && take(j)) val = (mode == 0) ? V[l * ld + j] / sqrt(ev[j]) : V[l * ld + j];
     Ms[idx] = val;
   }
   if (threadIdx.x == 0 && kept) {
     int c = 0;
-    for (int j = 0; j < n; ++j) {
-      if (mode == 0)
-        c += (l0 > 0.0 && ev[j] > rel * l0) ? 1 : 0;
-      else
-        c += (j < keep) ? 1 : 0;
-    }
+    for (int j = 0; j < n; ++j) c += take(j) ? 1 : 0;
     kept[sd] = c;
   }
 }
@@ -309,10 +303,11 @@ void launch_sym_eig(int n_sd, const double* A, int ld, int n, double* evals,
 }
 
 void launch_make_M(int n_sd, int mode, const double* evals, const double* evecs, int ld,
-                   int n, double rel, int keep, double* M, int* kept, cudaStream_t st) {
+                   int n, double rel, int keep, double* M, int* kept, cudaStream_t st,
+                   const int32_t* keep_sd) {
   if (n_sd <= 0) return;
   count_launch();
-  k_make_M<<<n_sd, 256, 0, st>>>(mode, evals, evecs, ld, n, rel, keep, M, kept);
+  k_make_M<<<n_sd, 256, 0, st>>>(mode, evals, evecs, ld, n, rel, keep, M, kept, keep_sd);
 }
 
 void launch_rowmul(const DTiles& tiles, const double* X, int ldx, int nin, const double* M,

@@ -33,13 +33,14 @@ void launch_assemble(int64_t n_rows, const int64_t* inc_ptr, const int32_t* inc_
 void launch_elem_lrow(int64_t n_inc, const int32_t* inc_tet, const uint32_t* inc_code,
                       const double* xyz, const int32_t* tets, double* lrow, cudaStream_t st);
 
-// out[r, j] = sum over incident elements T of (L_T xi_T[:, j])[a(r)], j < k, for rows
-// [row0, row0 + n_rows); xi from Philox counter (T, j, row_sd[r], 0).  fast = binary32
-// accumulation (the normals are identical either way).
+// out[r, j] = sum over incident elements T of (L_T xi_T[:, j])[a(r)], j < k_sd[row_sd[r]]
+// (or j < k when k_sd is null), zero for the other j < k, for rows [row0, row0 + n_rows);
+// xi from Philox counter (T, j, row_sd[r], 0).  fast = binary32 accumulation (the
+// normals are identical either way).
 void launch_sketch_rhs(bool fast, int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int64_t* inc_ptr, const int32_t* inc_tet,
                        const uint32_t* inc_code, const double* lrow, int k, uint64_t seed,
-                       double* out, int ld, cudaStream_t st);
+                       double* out, int ld, cudaStream_t st, const int32_t* k_sd);
 
 // Extract a sliced-ELL matrix from an assembled pattern: destination row r takes source
 // row s = row_src ? row_src[r] : r when row_cls is null or row_cls[s] == row_want;
@@ -91,9 +92,11 @@ void launch_spmm(const DTiles& tiles, const EllView<T>& A, const T* X, T* Y, int
                  cudaStream_t st);
 
 // Jacobi-preconditioned CG, independent per (subdomain, column), one step = 3 kernels.
+// columns c < ncn of a subdomain measure convergence against the largest ||b_c|| among
+// them (block-normwise); the others against their own ||b_c||
 template <typename T>
 void launch_cg_init(const DTiles& tiles, const T* b, T* x, T* r, T* p, const T* dinv,
-                    int kp, int nc, const CgState& s, cudaStream_t st);
+                    int kp, int nc, int ncn, const CgState& s, cudaStream_t st);
 // ev (null or 4 events) is recorded before the sparse product and after each of the
 // three kernels of the step.
 template <typename T>
@@ -111,7 +114,7 @@ struct RefineState {
   int* active;                // n_sd
 };
 void launch_residual64(const DTiles& tiles, const EllView<double>& A, const double* b64,
-                       const double* x64, double* r64, int kp, int nc, double rtol2,
+                       const double* x64, double* r64, int kp, int nc, int ncn, double rtol2,
                        int first, const RefineState& s, cudaStream_t st);
 void launch_zero_rows(const DTiles& tiles, double* x, int kp, cudaStream_t st);
 // residual replacement of the CG recursion: rT = (T) r64, rz recomputed, done flags from
@@ -119,7 +122,8 @@ void launch_zero_rows(const DTiles& tiles, double* x, int kp, cudaStream_t st);
 // reopened columns restart with pT = D^{-1} rT
 template <typename T>
 void launch_cg_replace(const DTiles& tiles, const double* r64, T* rT, T* pT, const T* dinv,
-                       int kp, const CgState& s, const RefineState& rs, cudaStream_t st);
+                       int kp, double drift, const CgState& s, const RefineState& rs,
+                       cudaStream_t st);
 // x64 += xT, xT = 0
 template <typename T>
 void launch_accum_reset(const DTiles& tiles, T* xT, double* x64, int kp, cudaStream_t st);
@@ -140,9 +144,11 @@ void launch_gram(const DTiles& tiles, int n_sd, const double* X, int ldx, int nx
 void launch_sym_eig(int n_sd, const double* A, int ld, int n, double* evals,
                     double* evecs, cudaStream_t st);
 // M[sd] from an eigen-decomposition: mode 0: V_j / sqrt(l_j) for l_j > rel * l_0 (else 0
-// column); mode 1: V_j for j < keep; kept[sd] = number of nonzero columns.
+// column); mode 1: V_j for j < keep (or j < keep_sd[sd]); mode 2: V_j for l_j > rel
+// (absolute), j < keep and j < keep_sd[sd]; kept[sd] = number of nonzero columns.
 void launch_make_M(int n_sd, int mode, const double* evals, const double* evecs, int ld,
-                   int n, double rel, int keep, double* M, int* kept, cudaStream_t st);
+                   int n, double rel, int keep, double* M, int* kept, cudaStream_t st,
+                   const int32_t* keep_sd = nullptr);
 // Y[r, j] = sum_{l < nin} X[r, l] M[sd(r)][l, j] for j < nout; columns nout..ldy-1 of Y
 // are zeroed.
 void launch_rowmul(const DTiles& tiles, const double* X, int ldx, int nin, const double* M,

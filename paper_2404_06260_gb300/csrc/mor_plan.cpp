@@ -4,6 +4,7 @@
 #include "mor_plan.h"
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <thread>
 
@@ -164,8 +165,8 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     err = "mor_build_subdomains: mesh too large for int32 indices";
     return MOR_ERR_ARG;
   }
-  if (r_hops < 1) {
-    err = "mor_build_subdomains: r_hops must be >= 1";
+  if (r_hops == 0 || r_hops < -1) {
+    err = "mor_build_subdomains: r_hops must be >= 1, or -1 for the per-subdomain rule";
     return MOR_ERR_ARG;
   }
   for (int64_t q = 0; q < 4 * n_tets; ++q)
@@ -209,6 +210,12 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
 
   int n_threads = (int)std::max(1u, std::thread::hardware_concurrency());
   n_threads = std::min(n_threads, 32);
+  // hops per subdomain: fixed, or about half the width of the owned set
+  // (max(1, round(cbrt(|P_i|) / 2)): the extension roughly doubles the diameter)
+  hp.r_sd.resize(n_sd);
+  for (int i = 0; i < n_sd; ++i)
+    hp.r_sd[i] = r_hops > 0 ? r_hops
+                            : std::max(1, (int32_t)std::lround(std::cbrt((double)P[i].size()) / 2.0));
   std::vector<Scratch> scratch(std::min(n_threads, n_sd));
   for (auto& s : scratch) s.init(n_nodes, n_tets);
   hp.sets.resize(n_sd);
@@ -224,7 +231,7 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     // r-hop ball of P_i over element edges
     std::vector<int32_t> ball_list = P[i], frontier = P[i], next;
     for (int32_t v : P[i]) S.ball[v] = st;
-    for (int h = 0; h < r_hops; ++h) {
+    for (int h = 0; h < hp.r_sd[i]; ++h) {
       next.clear();
       for (int32_t v : frontier)
         for (int64_t q = n2t_ptr[v]; q < n2t_ptr[v + 1]; ++q)

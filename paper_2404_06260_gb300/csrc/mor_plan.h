@@ -34,7 +34,8 @@ struct SubSets {
 struct HostPlan {
   int64_t n_nodes = 0, n_tets = 0;
   int32_t n_sd = 0;
-  int32_t r_hops = 0;
+  int32_t r_hops = 0;           // < 0: per-subdomain rule, see r_sd
+  std::vector<int32_t> r_sd;    // hops used for each subdomain
   std::vector<SubSets> sets;
   // batched row spaces: P (I then B rows of every omega_i^+), W (free nodes of every
   // omega_i), O (owned free nodes)

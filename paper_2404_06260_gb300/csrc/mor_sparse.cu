@@ -267,7 +267,7 @@ __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
 
 __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restrict__ b,
                              const double* __restrict__ x, double* __restrict__ r, int kp,
-                             int nc, double rtol2, int first, RefineState s) {
+                             int nc, int ncn, double rtol2, int first, RefineState s) {
   constexpr int N = 2;
   Geo g = geo();
   Smem<double> sm = smem_layout<double>(g, kp, A.W);
@@ -293,12 +293,19 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
   if (!last_block(g, s.counter, sd, hi - lo)) return;
   sd_colsums(g, s.part, kp, lo, hi, sm.scratch, sm.sums);
   __shared__ int cnt;
-  if (g.tid == 0) cnt = 0;
+  __shared__ double bref;
+  if (g.tid == 0) {
+    cnt = 0;
+    double m = 0.0;
+    if (first)
+      for (int c = 0; c < ncn; ++c) m = fmax(m, sm.sums[c]);
+    bref = m;
+  }
   __syncthreads();
   for (int c = g.tid; c < kp; c += g.nth) {
     int i = sd * kp + c;
     double rr = sm.sums[c];
-    if (first) s.obb[i] = rr;
+    if (first) s.obb[i] = (c < ncn) ? bref : rr;
     s.orr[i] = rr;
     bool done = (c >= nc) || !(s.obb[i] > 0.0) || rr <= rtol2 * s.obb[i];
     s.scale[i] = done ? 0.0 : 1.0 / sqrt(rr);
@@ -310,7 +317,7 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
 
 template <typename T>
 __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r, T* p,
-                          const T* __restrict__ dinv, int kp, int nc, CgState s) {
+                          const T* __restrict__ dinv, int kp, int nc, int ncn, CgState s) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
@@ -343,11 +350,18 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r, T* p,
   if (!last_block(g, s.counter, sd, hi - lo)) return;
   sd_colsums(g, s.part1, kp, lo, hi, sm.scratch, sm.sums);
   sd_colsums(g, s.part2, kp, lo, hi, sm.scratch, sm.sums + kp);
+  __shared__ double bref;
+  if (g.tid == 0) {
+    double m = 0.0;
+    for (int c = 0; c < ncn; ++c) m = fmax(m, sm.sums[kp + c]);
+    bref = m;
+  }
+  __syncthreads();
   for (int c = g.tid; c < kp; c += g.nth) {
     int i = sd * kp + c;
     double bb = sm.sums[kp + c];
     s.rz[i] = sm.sums[c];
-    s.bb[i] = bb;
+    s.bb[i] = (c < ncn) ? bref : bb;
     s.rr[i] = bb;
     s.done[i] = (c >= nc || !(bb > 0.0)) ? 1 : 0;
     s.alpha[i] = 0.0;
@@ -458,12 +472,12 @@ __global__ void k_zero_rows(DTiles tl, double* x, int kp) {
 // residual replacement: rT = (T) r64 (the true residual), rz recomputed from it, and
 // each column's done flag taken from the binary64 convergence test (scale == 0)
 // Columns the recursion had declared converged but the binary64 test reopens, and
-// columns whose true residual exceeds 1.5x the recursive one, restart from
+// columns whose true residual norm exceeds drift x the recursive one, restart from
 // p = D^{-1} r: their stored direction belongs to a much smaller residual.
 template <typename T>
 __global__ void k_cg_replace(DTiles tl, const double* __restrict__ r64, T* __restrict__ rT,
-                             T* __restrict__ pT, const T* __restrict__ dinv, int kp, CgState s,
-                             RefineState rs) {
+                             T* __restrict__ pT, const T* __restrict__ dinv, int kp,
+                             double drift2, CgState s, RefineState rs) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
@@ -475,7 +489,7 @@ __global__ void k_cg_replace(DTiles tl, const double* __restrict__ r64, T* __res
     int i = sd * kp + g.tx * N + e;
     // reopened, or the recursion drifted from the true residual (a stale direction
     // would make the next step length meaningless)
-    restart[e] = rs.scale[i] != 0.0 && (s.done[i] || rs.orr[i] > 2.25 * s.rr[i]);
+    restart[e] = rs.scale[i] != 0.0 && (s.done[i] || rs.orr[i] > drift2 * s.rr[i]);
   }
   T arz[N];
 #pragma unroll
@@ -564,12 +578,12 @@ void launch_spmm(const DTiles& tiles, const EllView<T>& A, const T* X, T* Y, int
 
 template <typename T>
 void launch_cg_init(const DTiles& tiles, const T* b, T* x, T* r, T* p, const T* dinv,
-                    int kp, int nc, const CgState& s, cudaStream_t st) {
+                    int kp, int nc, int ncn, const CgState& s, cudaStream_t st) {
   if (tiles.n <= 0) return;
   dim3 bl = block_of<T>(kp);
   count_launch();
   k_cg_init<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, b, x, r, p, dinv,
-                                                                      kp, nc, s);
+                                                                      kp, nc, ncn, s);
 }
 
 template <typename T>
@@ -601,7 +615,7 @@ void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st)
 }
 
 void launch_residual64(const DTiles& tiles, const EllView<double>& A, const double* b64,
-                       const double* x64, double* r64, int kp, int nc, double rtol2,
+                       const double* x64, double* r64, int kp, int nc, int ncn, double rtol2,
                        int first, const RefineState& s, cudaStream_t st) {
   if (tiles.n <= 0) return;
   static bool attr = false;
@@ -612,17 +626,18 @@ void launch_residual64(const DTiles& tiles, const EllView<double>& A, const doub
   dim3 bl = block_of<double>(kp);
   count_launch();
   k_residual64<<<tiles.n, bl, smem_bytes<double>(bl.x, bl.y, kp, A.W), st>>>(
-      tiles, A, b64, x64, r64, kp, nc, rtol2, first, s);
+      tiles, A, b64, x64, r64, kp, nc, ncn, rtol2, first, s);
 }
 
 template <typename T>
 void launch_cg_replace(const DTiles& tiles, const double* r64, T* rT, T* pT, const T* dinv,
-                       int kp, const CgState& s, const RefineState& rs, cudaStream_t st) {
+                       int kp, double drift, const CgState& s, const RefineState& rs,
+                       cudaStream_t st) {
   if (tiles.n <= 0) return;
   dim3 bl = block_of<T>(kp);
   count_launch();
-  k_cg_replace<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, r64, rT, pT,
-                                                                         dinv, kp, s, rs);
+  k_cg_replace<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(
+      tiles, r64, rT, pT, dinv, kp, drift * drift, s, rs);
 }
 
 template <typename T>
@@ -640,11 +655,11 @@ void launch_cast(const DTiles& tiles, const double* src, T* dst, int kp, cudaStr
 }
 
 template void launch_cg_replace<float>(const DTiles&, const double*, float*, float*,
-                                       const float*, int, const CgState&, const RefineState&,
-                                       cudaStream_t);
+                                       const float*, int, double, const CgState&,
+                                       const RefineState&, cudaStream_t);
 template void launch_cg_replace<double>(const DTiles&, const double*, double*, double*,
-                                        const double*, int, const CgState&, const RefineState&,
-                                        cudaStream_t);
+                                        const double*, int, double, const CgState&,
+                                        const RefineState&, cudaStream_t);
 template void launch_accum_reset<float>(const DTiles&, float*, double*, int, cudaStream_t);
 template void launch_accum_reset<double>(const DTiles&, double*, double*, int, cudaStream_t);
 template void launch_cast<float>(const DTiles&, const double*, float*, int, cudaStream_t);
@@ -661,9 +676,10 @@ template void launch_spmm<float>(const DTiles&, const EllView<float>&, const flo
 template void launch_spmm<double>(const DTiles&, const EllView<double>&, const double*,
                                   double*, int, cudaStream_t);
 template void launch_cg_init<float>(const DTiles&, const float*, float*, float*, float*,
-                                    const float*, int, int, const CgState&, cudaStream_t);
+                                    const float*, int, int, int, const CgState&, cudaStream_t);
 template void launch_cg_init<double>(const DTiles&, const double*, double*, double*, double*,
-                                     const double*, int, int, const CgState&, cudaStream_t);
+                                     const double*, int, int, int, const CgState&,
+                                     cudaStream_t);
 template void launch_cg_step<float>(const DTiles&, const EllView<float>&, float*, float*,
                                     float*, float*, const float*, int, double, const CgState&,
                                     cudaStream_t, const cudaEvent_t*);

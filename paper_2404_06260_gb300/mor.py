@@ -34,9 +34,11 @@ class _MeshC(ctypes.Structure):
 
 
 class BasisOpts(ctypes.Structure):
-    _fields_ = [("rank", _i32), ("oversample", _i32), ("seed", ctypes.c_uint64),
+    _fields_ = [("rank", _i32), ("oversample", _i32), ("ranks", _P), ("eps", _dbl),
+                ("seed", ctypes.c_uint64),
                 ("precision", _i32), ("sketch", _i32), ("cg_rtol", _dbl),
-                ("max_iter", _i32), ("replace_every", _i32),
+                ("max_iter", _i32), ("replace_every", _i32), ("normwise", _i32),
+                ("drift_restart", _dbl),
                 ("sketch_rtol", _dbl), ("tau", _dbl), ("orth_tol", _dbl)]
 
 
@@ -155,7 +157,7 @@ class Subdomains:
         n = _i32()
         _check(_lib.mor_subdomains_counts(h, ctypes.byref(n), None))
         self.n_sub = n.value
-        self.counts = np.zeros((self.n_sub, 6), dtype=np.int64)
+        self.counts = np.zeros((self.n_sub, 7), dtype=np.int64)
         _check(_lib.mor_subdomains_counts(h, None, _ptr(self.counts)))
 
     def indices(self, sub: int, which: int) -> np.ndarray:
@@ -170,11 +172,17 @@ class Subdomains:
 
 
 def basis_opts(**kw) -> BasisOpts:
+    """Defaults of mor_basis_opts_default overridden by keywords; `ranks` may be a
+    sequence of per-subdomain ranks (kept alive on the returned object)."""
     o = BasisOpts()
     _check(_lib.mor_basis_opts_default(ctypes.byref(o)))
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": FP64, "mixed": MIXED}[v]
+        if k == "ranks":
+            arr = np.ascontiguousarray(v, dtype=np.int32)
+            o._ranks = arr
+            v = _ptr(arr)
         setattr(o, k, v)
     return o
 

@@ -13,6 +13,7 @@ from .meshes import (  # noqa: F401
     sphere_kappa,
     box_owner,
     slab_owner,
+    kmeans_owner,
     workload,
     WORKLOADS,
 )

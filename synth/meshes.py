@@ -132,6 +132,33 @@ def slab_owner(n: int, parts: int, axis: int = 0) -> np.ndarray:
     return [ax, ay, az][axis].ravel().astype(np.int32)
 
 
+def kmeans_owner(mesh: Mesh, parts: int, seed: int, iters: int = 20,
+                 sample: int = 200000) -> np.ndarray:
+    """Owner labels from k-means on element centroids: Lloyd iterations (seeded
+    k-means++ start) on a seeded sample of `sample` centroids, then every node is owned
+    by its nearest centre.  Labels are renumbered 0..n-1 over the centres that own a
+    node."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    cen = mesh.xyz[mesh.tets].mean(axis=1)
+    pts = cen[rng.choice(len(cen), size=min(sample, len(cen)), replace=False)]
+    C = np.empty((parts, 3))
+    C[0] = pts[rng.integers(len(pts))]
+    d2 = np.sum((pts - C[0]) ** 2, axis=1)
+    for j in range(1, parts):
+        C[j] = pts[rng.choice(len(pts), p=d2 / d2.sum())]
+        d2 = np.minimum(d2, np.sum((pts - C[j]) ** 2, axis=1))
+    for _ in range(iters):
+        lab = cKDTree(C).query(pts)[1]
+        cnt = np.bincount(lab, minlength=parts)
+        for ax in range(3):
+            sums = np.bincount(lab, weights=pts[:, ax], minlength=parts)
+            C[cnt > 0, ax] = sums[cnt > 0] / cnt[cnt > 0]
+    owner = cKDTree(C).query(mesh.xyz)[1]
+    _, owner = np.unique(owner, return_inverse=True)
+    return owner.astype(np.int32)
+
+
 # Workloads (sizes of the paper's structured scaling meshes, Sec. 7.1, scaled down
 # for the small cases).  rank = kept singular vectors, oversample = extra sketch
 # columns, r_hops = extension hops (about half the subdomain width, so the extension
@@ -141,6 +168,9 @@ WORKLOADS = {
                       seed=1001),
     "cube64_p4": dict(n=64, parts=4, rank=32, oversample=10, r_hops=8, field="lognormal",
                       seed=1002),
+    "cube96_kmeans": dict(n=96, parts=300, rank=0, oversample=10, r_hops=-1,
+                          field="lognormal", seed=1003, jitter=0.2, partition="kmeans",
+                          rank_range=(16, 64)),
     "cube128_p8_spheres": dict(n=128, parts=8, rank=48, oversample=10, r_hops=8,
                                field="spheres", seed=1004),
     "cube440_p20": dict(n=440, parts=20, rank=32, oversample=10, r_hops=11,
@@ -149,15 +179,25 @@ WORKLOADS = {
 
 
 def workload(name: str, **override):
-    """Return (mesh, kappa, owner, params) for a named workload."""
+    """Return (mesh, kappa, owner, params) for a named workload.  For workloads with a
+    rank range, params["ranks"] holds the seeded per-subdomain ranks (uniform in the
+    range, inclusive) and params["r_hops"] = -1 selects the per-subdomain hop rule
+    max(1, round(|P_i|^(1/3) / 2))."""
     p = dict(WORKLOADS[name])
     p.update(override)
-    mesh = kuhn_cube(p["n"])
+    mesh = kuhn_cube(p["n"], jitter=p.get("jitter", 0.0), seed=p["seed"])
     if p["field"] == "lognormal":
         kappa = lognormal_kappa(mesh.n_tets, p["seed"])
     elif p["field"] == "ones":
         kappa = np.ones(mesh.n_tets)
     else:
         kappa = sphere_kappa(mesh, p["seed"])
-    owner = box_owner(p["n"], p["parts"])
+    if p.get("partition") == "kmeans":
+        owner = kmeans_owner(mesh, p["parts"], p["seed"])
+    else:
+        owner = box_owner(p["n"], p["parts"])
+    if "rank_range" in p:
+        lo, hi = p["rank_range"]
+        n_sub = int(owner.max()) + 1
+        p["ranks"] = np.random.default_rng(p["seed"] + 7).integers(lo, hi + 1, size=n_sub)
     return mesh, kappa, owner, p

@@ -1,0 +1,155 @@
+"""GPU path on the remaining workloads and on tolerance-mode truncation, against the
+oracle on sampled subdomains and against properties that hold at any size.
+
+- cube96_kmeans: an uneven batch. A 96^3 cube with interior nodes jittered by ±0.2h,
+  300 k-means subdomains (2k–4k owned nodes each), per-subdomain rank uniform in
+  16..64 (sketch width rank + 10), and per-subdomain hops round(|P_i|^(1/3)/2).
+- cube128_p8_spheres: high contrast. A 128^3 cube with k = 1e4 in seeded spheres
+  (≥10% of the elements), 512 box subdomains, rank 48 + 10.
+- Tolerance mode (Eq. (15)) on the 16^3 cube: keep sigma_j > eps. eps is placed in the
+  middle of a gap of the oracle's singular values, so the integer decision is not a
+  rounding tie; the binary64 path must then keep the same number of directions.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import basis as obasis
+from oracle import pipeline, reduced
+from oracle import subdomains as osub
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mor():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2404_06260_gb300 import _build
+    _build.build()
+    from paper_2404_06260_gb300 import mor as m
+    return m
+
+
+def _build_both(mor, sd, p, ranks=None):
+    out = {}
+    for prec, rt in (("fp64", 1e-11), ("mixed", 1e-9)):
+        kw = dict(rank=int(p["rank"]) if p["rank"] else 1, oversample=p["oversample"],
+                  seed=p["seed"], precision=prec, cg_rtol=rt)
+        if ranks is not None:
+            kw["ranks"] = ranks
+        b = mor.Bases(sd, mor.basis_opts(**kw))
+        assert b.converged, prec
+        r = mor.Reduced(sd, b)
+        x, info = r.solve(rtol=1e-12)
+        assert info["converged"], prec
+        out[prec] = (b, r, x, info, mor.lift(sd, b, x))
+    return out
+
+
+def _check_sampled(mesh, kappa, owner, p, sd, out, subs, rank_of):
+    adj = osub.node_adjacency(mesh.tets, mesh.n_nodes)
+    for i in subs:
+        s = osub.subdomain_sets(mesh, owner, i, p["r_hops"], adj)
+        for which, key in enumerate(["I", "B", "omega", "owned", "plus_tets", "omega_tets"]):
+            assert np.array_equal(sd.indices(i, which), s[key]), (i, key)
+        ob = obasis.local_basis(mesh, kappa, s, rank_of(i), p["oversample"], p["seed"])
+        m = rank_of(i)
+        ref = ob["sigma"]
+        gap = (ref[m - 1] - ref[m]) / ref[0]
+        A = ob["A_PP"]
+        for prec, tol in (("fp64", 1e-9), ("mixed", 1e-7)):
+            b = out[prec][0]
+            sig = b.sigma()[i]
+            n = len(ref)
+            assert np.max(np.abs(sig[:n] - ref[:n])) <= tol * ref[0], (i, prec)
+            assert np.all(sig[n:] == 0.0)
+            Qg = b.Q(i)[:, :b.kept[i]]
+            Qo = ob["Q"]
+            assert Qg.shape[1] == Qo.shape[1], (i, prec)
+            R = Qg - Qo @ (Qo.T @ (A @ Qg))
+            sin_max = np.sqrt(max(0.0, np.linalg.eigvalsh(R.T @ (A @ R)).max()))
+            assert sin_max <= tol / min(1.0, gap), (i, prec, sin_max, gap)
+
+
+def _check_batch(mor, sd, out):
+    # Galerkin identity of the stitched reduced system (Eq. (23)):
+    # ||u~||_A^2 = x^T K~ x = x^T b~ = E, with u~ the lifted solution (Eq. (11)).  A wrong
+    # interface block or load entry breaks it whatever the size.
+    for prec in ("fp64", "mixed"):
+        b, r, x, info, u = out[prec]
+        assert b.total_kept == int(b.kept.sum())
+        assert info["energy"] > 0
+        e2 = mor.energy_norm(sd, u) ** 2
+        assert abs(e2 - info["energy"]) <= 1e-8 * info["energy"], (prec, e2, info["energy"])
+    e = mor.energy_norm(sd, out["mixed"][4], out["fp64"][4]) / mor.energy_norm(sd, out["fp64"][4])
+    assert e <= 1e-6, e
+
+
+def test_uneven_kmeans_batch(mor):
+    mesh, kappa, owner, p = synth.workload("cube96_kmeans")
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, -1)
+    assert sd.n_sub == 300
+    ranks = p["ranks"]
+    # the per-subdomain hop rule of the library equals the oracle's
+    cnt = np.bincount(owner)
+    assert np.array_equal(sd.counts[:, 6], [osub.hops_for(c, -1) for c in cnt])
+    out = _build_both(mor, sd, p, ranks=ranks)
+    # every subdomain keeps u_0 plus its own m_i directions (none dropped here)
+    for prec in out:
+        assert np.all(out[prec][0].kept <= ranks + 1)
+        assert np.all(out[prec][0].kept >= ranks)
+    # sampled oracle checks: the smallest extended subdomains
+    sizes = sd.counts[:, 0] + sd.counts[:, 1]
+    subs = list(np.argsort(sizes)[:2])
+    _check_sampled(mesh, kappa, owner, p, sd, out, subs, lambda i: int(ranks[i]))
+    _check_batch(mor, sd, out)
+
+
+def test_high_contrast_spheres(mor):
+    mesh, kappa, owner, p = synth.workload("cube128_p8_spheres")
+    assert 0.10 <= np.mean(kappa > 1) < 0.2
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, p["r_hops"])
+    assert sd.n_sub == 512
+    out = _build_both(mor, sd, p)
+    _check_sampled(mesh, kappa, owner, p, sd, out, [0], lambda i: p["rank"])
+    _check_batch(mor, sd, out)
+
+
+def test_tolerance_mode_matches_oracle(mor):
+    mesh, kappa, owner, p = synth.workload("cube16_p2")
+    k = 13
+    ref0 = pipeline.run(mesh, kappa, owner, p["rank"], p["oversample"], p["r_hops"],
+                        p["seed"], fe_solution=False)
+    sig = np.sort(np.concatenate([b["sigma"][:k] for b in ref0["bases"]]))[::-1]
+    # eps at the geometric middle of a clear gap (ratio > 1.05) near the middle of the
+    # spectrum, so each subdomain keeps some but not all of its k directions and no
+    # sigma_j lies within rounding of eps
+    gaps = [j for j in range(len(sig) - 1) if sig[j] > 1.05 * sig[j + 1] and sig[j + 1] > 0]
+    j = min(gaps, key=lambda g: abs(g - len(sig) // 2))
+    eps = float(np.sqrt(sig[j] * sig[j + 1]))
+    ref = pipeline.run(mesh, kappa, owner, p["rank"], p["oversample"], p["r_hops"], p["seed"],
+                       eps=eps, fe_solution=False)
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, p["r_hops"])
+    b = mor.Bases(sd, mor.basis_opts(rank=p["rank"], oversample=p["oversample"],
+                                     seed=p["seed"], precision="fp64", cg_rtol=1e-13,
+                                     eps=eps))
+    assert b.converged
+    m_or = np.array([ob["m"] for ob in ref["bases"]])
+    assert np.all((m_or > 0) & (m_or < k))
+    # u_0 plus the sigma_j > eps, less any direction the tau test drops
+    assert np.array_equal(b.kept, [ob["n_kept"] for ob in ref["bases"]])
+    for i, ob in enumerate(ref["bases"]):
+        A = ob["A_PP"]
+        Qg = b.Q(i)[:, :b.kept[i]]
+        R = Qg - ob["Q"] @ (ob["Q"].T @ (A @ Qg))
+        assert np.sqrt(max(0.0, np.linalg.eigvalsh(R.T @ (A @ R)).max())) < 1e-8
+    r = mor.Reduced(sd, b)
+    x, info = r.solve(rtol=1e-14)
+    assert abs(info["energy"] - ref["E"]) <= 1e-10 * ref["E"]
+    u = mor.lift(sd, b, x).cpu().numpy()
+    assert reduced.energy_norm(mesh, kappa, u - ref["u_red"]) <= \
+        1e-10 * reduced.energy_norm(mesh, kappa, ref["u_red"])
