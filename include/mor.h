@@ -104,7 +104,10 @@ typedef struct {
   int32_t precision;   /* MOR_FP64 or MOR_MIXED                                         */
   int32_t sketch;      /* MOR_SKETCH_FIELD                                              */
   double cg_rtol;      /* every local solve: ||b - A x||_2 <= cg_rtol ||b||_2 per column,
-                          residual measured in binary64                                 */
+                          residual measured in binary64.  A column also stops when its
+                          residual is below 4 u || |A| |x| + |b| ||_2 (u = 2^-53), the
+                          rounding level of the binary64 residual itself: with high
+                          coefficient contrast a small cg_rtol can lie below it        */
   int32_t max_iter;    /* CG iterations per local solve                                 */
   int32_t replace_every; /* the CG residual is replaced by the binary64 residual
                           b - A x every replace_every iterations (rounded to a multiple
@@ -163,7 +166,8 @@ int mor_bases_get_bt(const mor_bases* h, double* out);
 
 /* Solver statistics of the last mor_build_bases: stats[host, 8] =
  * {iterations of the four local solves (sketch, forward, adjoint, H^+), residual
- * replacements (sum), columns not converged, 0, 0}. */
+ * replacements (sum), columns not converged, columns that stopped on the
+ * attainable-accuracy test instead of cg_rtol, 0}. */
 int mor_bases_stats(const mor_bases* h, int64_t* stats);
 
 /* Step 3a (Eq. (23), Sec. 6 step 3): K~ with identity diagonal blocks (from step 2) and
@@ -233,7 +237,8 @@ int mor_energy_norm(const mor_subdomains* sd, const double* u1_dev, const double
 
 /* Debug/parity access: the field-sketch right-hand side L xi of subdomain `sub`
  * (rows I then B, k columns, row-major) into out[host, (|I|+|B|) x k], computed by the
- * same kernel mor_build_bases uses (binary64 element factors). */
+ * same kernel mor_build_bases uses (binary32 Gaussian draws, binary64 element factors
+ * and sums, in every precision). */
 int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts,
                          int32_t sub, double* out, void* stream);
 

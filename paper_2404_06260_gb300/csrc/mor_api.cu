@@ -344,7 +344,7 @@ struct Build {
   CgState cs{};
   RefineState rs{};
   int64_t iters[4] = {0, 0, 0, 0};
-  int64_t sweeps = 0, not_conv = 0;
+  int64_t sweeps = 0, not_conv = 0, floor_cols = 0;
   bool debug = getenv("MOR_DEBUG") != nullptr;
   ~Build() {
     if (h_poll) cudaFreeHost(h_poll);
@@ -381,13 +381,13 @@ struct Build {
     // replace_every iterations and whenever the recursion reports convergence
     // (residual replacement keeps the search directions, so no Krylov restart)
     launch_zero_rows(tl, x64, kp, st);
-    launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 1, rs, st);
+    launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 1, false, rs, st);
     if (poll(rs.active) == 0) return MOR_OK;
     launch_cast<T>(tl, vR64, b, kp, st);
     launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, ncn, cs, st);
     const int check = 8;
     const int every = std::max(check, o->replace_every / check * check);
-    int it = 0;
+    int it = 0, nsweep = 0;
     while (true) {
       int chunk = std::min(check, o->max_iter - it);
       for (int c = 0; c < chunk; ++c) {
@@ -403,7 +403,10 @@ struct Build {
       int act = poll(cs.active);
       if (act == 0 || it % every == 0 || it >= o->max_iter) {
         launch_accum_reset<T>(tl, x, x64, kp, st);
-        launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 0, rs, st);
+        // the rounding-level reference is refreshed on sweeps 1, 2, 4, 8, ...
+        ++nsweep;
+        const bool refresh = (nsweep & (nsweep - 1)) == 0;
+        launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 0, refresh, rs, st);
         ++sweeps;
         int ract = poll(rs.active);
         if (debug) {
@@ -420,9 +423,14 @@ struct Build {
           fprintf(stderr, "[mor] solve %d it %d active %d recursive-active %d worst %.3e (sd %d col %d)\n",
                   which, it, ract, act, std::sqrt(worst), wi / kp, wi % kp);
         }
-        if (ract == 0) break;
-        if (it >= o->max_iter) {
-          not_conv += ract;
+        if (ract == 0 || it >= o->max_iter) {
+          // columns that ended on the attainable-accuracy test instead of rtol
+          std::vector<int> nfl(n_sd);
+          CK(cudaMemcpyAsync(nfl.data(), rs.nfloor, n_sd * sizeof(int), cudaMemcpyDeviceToHost,
+                             st));
+          CK(cudaStreamSynchronize(st));
+          for (int v : nfl) floor_cols += v;
+          if (ract > 0) not_conv += ract;
           break;
         }
         launch_cg_replace<T>(tl, vR64, r, p, dinvT, kp, o->drift_restart, cs, rs, st);
@@ -635,6 +643,9 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.alloc(&B.rs.orr, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.rs.scale, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.rs.part, (size_t)mt * kp, true, st));
+  TRY(M.alloc(&B.rs.part2, (size_t)mt * kp, true, st));
+  TRY(M.alloc(&B.rs.oaa, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.rs.nfloor, n_sd, true, st));
   TRY(M.alloc(&B.rs.counter, n_sd, true, st));
   TRY(M.alloc(&B.rs.active, n_sd, true, st));
   double *Xw, *Yw, *Zw, *u0w, *V, *AV, *bP;
@@ -684,7 +695,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.upload(&d_ksd, h_k, st));
   TRY(M.upload(&d_msd, h_rank, st));
   TRY(M.alloc(&d_msel, n_sd, true, st));
-  launch_sketch_rhs(B.mixed, 0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lrow, k, o.seed,
+  launch_sketch_rhs(0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lrow, k, o.seed,
                     vS, kp, st, d_ksd);
   TRY(solve(S.tP_all, Hp, false, vS, vG, k, 0, rt_sketch));
 
@@ -752,6 +763,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   Bo.stats[3] = B.iters[3];
   Bo.stats[4] = B.sweeps;
   Bo.stats[5] = B.not_conv;
+  Bo.stats[6] = B.floor_cols;
   *out = bases.release();
   if (B.not_conv > 0)
     return fail(MOR_ERR_NOT_CONVERGED, "mor_build_bases: " + std::to_string(B.not_conv) +
@@ -953,7 +965,7 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, i
   TRY(A.alloc(&lrow, nInc * 4, false, st));
   TRY(A.alloc(&res, (hp.nP) * (size_t)k, true, st));
   launch_elem_lrow(nInc, sd->incP_tet, sd->incP_code, sd->xyz, sd->tets, lrow, st);
-  launch_sketch_rhs(opts->precision == MOR_MIXED, row0, n_rows, sd->p_sd, sd->incP_ptr,
+  launch_sketch_rhs(row0, n_rows, sd->p_sd, sd->incP_ptr,
                     sd->incP_tet, sd->incP_code, lrow, k, opts->seed, res, k, st, nullptr);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, res + row0 * k, n_rows * k * sizeof(double), cudaMemcpyDeviceToHost, st));

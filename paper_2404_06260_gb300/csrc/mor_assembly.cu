@@ -92,8 +92,9 @@ void launch_elem_lrow(int64_t n_inc, const int32_t* inc_tet, const uint32_t* inc
                                                                  xyz, tets, lrow);
 }
 
-// one warp per row, lanes over columns
-template <bool kFast>
+// one warp per row, lanes over columns.  The Gaussian draws are binary32 (bit-exact
+// Box-Muller); the sums over element incidences are binary64 whatever the solve
+// precision, so every precision sketches with the same test matrix W
 __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __restrict__ row_sd,
                              const int64_t* __restrict__ inc_ptr,
                              const int32_t* __restrict__ inc_tet,
@@ -110,24 +111,18 @@ __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __rest
   for (int j = lane + kk; j < k; j += 32) out[r * ld + j] = 0.0;
   for (int j = lane; j < kk; j += 32) {
     double acc = 0.0;
-    float accf = 0.0f;
     for (int64_t q = q0; q < q1; ++q) {
       float z[4];
       field_normals((uint32_t)inc_tet[q], (uint32_t)j, sd, seed, z);
       const double* L = lrow + 4 * q;
-      if (kFast) {
-        accf += (float)L[0] * z[0] + (float)L[1] * z[1] + (float)L[2] * z[2] +
-                (float)L[3] * z[3];
-      } else {
-        acc += L[0] * (double)z[0] + L[1] * (double)z[1] + L[2] * (double)z[2] +
-               L[3] * (double)z[3];
-      }
+      acc += L[0] * (double)z[0] + L[1] * (double)z[1] + L[2] * (double)z[2] +
+             L[3] * (double)z[3];
     }
-    out[r * ld + j] = kFast ? (double)accf : acc;
+    out[r * ld + j] = acc;
   }
 }
 
-void launch_sketch_rhs(bool fast, int64_t row0, int64_t n_rows, const int32_t* row_sd,
+void launch_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int64_t* inc_ptr, const int32_t* inc_tet,
                        const uint32_t* inc_code, const double* lrow, int k, uint64_t seed,
                        double* out, int ld, cudaStream_t st, const int32_t* k_sd) {
@@ -136,12 +131,8 @@ void launch_sketch_rhs(bool fast, int64_t row0, int64_t n_rows, const int32_t* r
   int bs = 256;
   unsigned grid = (unsigned)((n_rows * 32 + bs - 1) / bs);
   count_launch();
-  if (fast)
-    k_sketch_rhs<true><<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, lrow, k,
-                                            seed, out, ld, k_sd);
-  else
-    k_sketch_rhs<false><<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, lrow, k,
-                                             seed, out, ld, k_sd);
+  k_sketch_rhs<<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, lrow, k, seed, out,
+                                    ld, k_sd);
 }
 
 // one thread per destination row; warps cover whole slices so the slice width is a

@@ -35,9 +35,8 @@ void launch_elem_lrow(int64_t n_inc, const int32_t* inc_tet, const uint32_t* inc
 
 // out[r, j] = sum over incident elements T of (L_T xi_T[:, j])[a(r)], j < k_sd[row_sd[r]]
 // (or j < k when k_sd is null), zero for the other j < k, for rows [row0, row0 + n_rows);
-// xi from Philox counter (T, j, row_sd[r], 0).  fast = binary32 accumulation (the
-// normals are identical either way).
-void launch_sketch_rhs(bool fast, int64_t row0, int64_t n_rows, const int32_t* row_sd,
+// xi from Philox counter (T, j, row_sd[r], 0), summed in binary64.
+void launch_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int64_t* inc_ptr, const int32_t* inc_tet,
                        const uint32_t* inc_code, const double* lrow, int k, uint64_t seed,
                        double* out, int ld, cudaStream_t st, const int32_t* k_sd);
@@ -109,13 +108,22 @@ void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st)
 // columns with ||r64|| > rtol ||b64|| (0 = converged); first = 1 records ||b64||.
 struct RefineState {
   double *obb, *orr, *scale;  // n_sd x kp
-  double* part;               // n_tiles x kp
+  double* oaa;                // n_sd x kp: || |A| |x| + |b| ||^2 at the last refresh
+  double *part, *part2;       // n_tiles x kp
   int* counter;               // n_sd
   int* active;                // n_sd
+  int* nfloor;                // n_sd: columns stopped by the attainable-accuracy test
 };
+// a binary64 residual below kResidualFloor * 2^-53 * || |A| |x| + |b| ||_2 is rounding
+// noise of its own evaluation; launch_residual64 stops such columns
+constexpr double kResidualFloor = 4.0;
+// r64 = b - A x64 per column, the binary64 convergence test (rtol, or the rounding level
+// of the residual itself), done flags in s.scale; first = 1 also fixes the references
+// from b (x64 = 0).  floor_ref = true refreshes the rounding-level reference
+// || |A| |x| + |b| || (one extra binary64 add per product)
 void launch_residual64(const DTiles& tiles, const EllView<double>& A, const double* b64,
                        const double* x64, double* r64, int kp, int nc, int ncn, double rtol2,
-                       int first, const RefineState& s, cudaStream_t st);
+                       int first, bool floor_ref, const RefineState& s, cudaStream_t st);
 void launch_zero_rows(const DTiles& tiles, double* x, int kp, cudaStream_t st);
 // residual replacement of the CG recursion: rT = (T) r64, rz recomputed, done flags from
 // the binary64 convergence test of launch_residual64 (scale == 0 means converged);

@@ -225,6 +225,42 @@ __global__ void k_spmm(DTiles tl, EllView<T> A, const T* __restrict__ X, T* __re
   }
 }
 
+// binary64 residual row: A x and sum_j |a_ij x_j| in one pass over the staged slots
+__device__ __forceinline__ void spmm_row_res(int rr, int w, int W, int tx, const int32_t* scol,
+                                             const double* sval, const double* __restrict__ X,
+                                             int kp, Pack<double>& acc, Pack<double>& aabs) {
+  constexpr int N = Pack<double>::N;
+  constexpr int U = 8;
+#pragma unroll
+  for (int e = 0; e < N; ++e) acc.v[e] = aabs.v[e] = 0.0;
+  const int32_t* cr = scol + rr * W;
+  const double* vr = sval + rr * W;
+  for (int j0 = 0; j0 < w; j0 += U) {
+    Pack<double> xv[U];
+    double av[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int j = j0 + u;
+      int32_t c = (j < w) ? cr[j] : -1;
+      av[u] = (j < w) ? vr[j] : 0.0;
+      if (c >= 0) {
+        xv[u] = ld(X + (int64_t)c * kp + tx * N);
+      } else {
+#pragma unroll
+        for (int e = 0; e < N; ++e) xv[u].v[e] = 0.0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < N; ++e) {
+        double t = av[u] * xv[u].v[e];
+        acc.v[e] += t;
+        aabs.v[e] += fabs(t);
+      }
+  }
+}
+
 template <typename T>
 __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
                              T* __restrict__ q, int kp, CgState s) {
@@ -265,6 +301,7 @@ __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
   }
 }
 
+template <bool kFloor>
 __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restrict__ b,
                              const double* __restrict__ x, double* __restrict__ r, int kp,
                              int nc, int ncn, double rtol2, int first, RefineState s) {
@@ -275,44 +312,76 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
   const int r0 = tl.r0[tile], r1 = tl.r1[tile];
   stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
   __syncthreads();
-  double acc[N] = {0.0, 0.0};
+  double acc[N] = {0.0, 0.0}, aca[N] = {0.0, 0.0};
   for (int rr = g.ty; rr < r1 - r0; rr += g.rb) {
     int64_t row = r0 + rr;
-    Pack<double> ax = spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, x, kp);
+    Pack<double> ax, aabs;
+    if constexpr (kFloor)
+      spmm_row_res(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, x, kp, ax, aabs);
+    else
+      ax = spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, x, kp);
     int64_t o = row * kp + g.tx * N;
     Pack<double> bv = ld(b + o), rv;
 #pragma unroll
     for (int e = 0; e < N; ++e) {
       rv.v[e] = bv.v[e] - ax.v[e];
       acc[e] += rv.v[e] * rv.v[e];
+      if constexpr (kFloor) {
+        double f = aabs.v[e] + fabs(bv.v[e]);
+        aca[e] += f * f;
+      }
     }
     st(r + o, rv);
   }
   block_colsum<double, N>(g, acc, sm.red, s.part + (int64_t)tile * kp);
+  if constexpr (kFloor) {
+    __syncthreads();
+    block_colsum<double, N>(g, aca, sm.red, s.part2 + (int64_t)tile * kp);
+  }
   const int lo = tl.lo[sd], hi = tl.hi[sd];
   if (!last_block(g, s.counter, sd, hi - lo)) return;
   sd_colsums(g, s.part, kp, lo, hi, sm.scratch, sm.sums);
-  __shared__ int cnt;
+  if constexpr (kFloor) {
+    sd_colsums(g, s.part2, kp, lo, hi, sm.scratch, sm.sums + kp);
+    for (int c = g.tid; c < kp; c += g.nth) s.oaa[sd * kp + c] = sm.sums[kp + c];
+  }
+  __shared__ int cnt, nfl;
   __shared__ double bref;
   if (g.tid == 0) {
     cnt = 0;
+    nfl = 0;
     double m = 0.0;
     if (first)
       for (int c = 0; c < ncn; ++c) m = fmax(m, sm.sums[c]);
     bref = m;
   }
   __syncthreads();
+  // attainable accuracy: the rounding error of the binary64 residual of a binary64 x is
+  // about u || |A| |x| + |b| ||_2 (u = 2^-53); a residual below kResidualFloor times that
+  // is rounding noise, so the column stops there even if rtol is not reached.  The
+  // reference (oaa, squared) is refreshed only by the kFloor sweeps; it is a scale,
+  // and zero (no floor test) until the first of them
+  const double fl2 = (kResidualFloor * 0x1p-53) * (kResidualFloor * 0x1p-53);
   for (int c = g.tid; c < kp; c += g.nth) {
     int i = sd * kp + c;
     double rr = sm.sums[c];
-    if (first) s.obb[i] = (c < ncn) ? bref : rr;
+    if (first) {
+      s.obb[i] = (c < ncn) ? bref : rr;
+      s.oaa[i] = 0.0;
+    }
     s.orr[i] = rr;
-    bool done = (c >= nc) || !(s.obb[i] > 0.0) || rr <= rtol2 * s.obb[i];
+    bool by_rtol = rr <= rtol2 * s.obb[i];
+    bool by_floor = rr <= fl2 * s.oaa[i];
+    bool done = (c >= nc) || !(s.obb[i] > 0.0) || by_rtol || by_floor;
     s.scale[i] = done ? 0.0 : 1.0 / sqrt(rr);
     if (!done) atomicAdd(&cnt, 1);
+    if (c < nc && s.obb[i] > 0.0 && !by_rtol && by_floor) atomicAdd(&nfl, 1);
   }
   __syncthreads();
-  if (g.tid == 0) s.active[sd] = cnt;
+  if (g.tid == 0) {
+    s.active[sd] = cnt;
+    s.nfloor[sd] = nfl;
+  }
 }
 
 template <typename T>
@@ -616,17 +685,23 @@ void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st)
 
 void launch_residual64(const DTiles& tiles, const EllView<double>& A, const double* b64,
                        const double* x64, double* r64, int kp, int nc, int ncn, double rtol2,
-                       int first, const RefineState& s, cudaStream_t st) {
+                       int first, bool floor_ref, const RefineState& s, cudaStream_t st) {
   if (tiles.n <= 0) return;
   static bool attr = false;
   if (!attr) {
-    set_smem_attr<double>((const void*)k_residual64);
+    set_smem_attr<double>((const void*)k_residual64<false>);
+    set_smem_attr<double>((const void*)k_residual64<true>);
     attr = true;
   }
   dim3 bl = block_of<double>(kp);
+  size_t sm = smem_bytes<double>(bl.x, bl.y, kp, A.W);
   count_launch();
-  k_residual64<<<tiles.n, bl, smem_bytes<double>(bl.x, bl.y, kp, A.W), st>>>(
-      tiles, A, b64, x64, r64, kp, nc, ncn, rtol2, first, s);
+  if (floor_ref && !first)
+    k_residual64<true><<<tiles.n, bl, sm, st>>>(tiles, A, b64, x64, r64, kp, nc, ncn, rtol2,
+                                                first, s);
+  else
+    k_residual64<false><<<tiles.n, bl, sm, st>>>(tiles, A, b64, x64, r64, kp, nc, ncn, rtol2,
+                                                 first, s);
 }
 
 template <typename T>

@@ -5,7 +5,7 @@ oracle on sampled subdomains and against properties that hold at any size.
   300 k-means subdomains (2k–4k owned nodes each), per-subdomain rank uniform in
   16..64 (sketch width rank + 10), and per-subdomain hops round(|P_i|^(1/3)/2).
 - cube128_p8_spheres: high contrast. A 128^3 cube with k = 1e4 in seeded spheres
-  (≥10% of the elements), 512 box subdomains, rank 48 + 10.
+  (≥10% of the elements), 512 box subdomains, rank 48 + 10; local solves to 1e-11.
 - Tolerance mode (Eq. (15)) on the 16^3 cube: keep sigma_j > eps. eps is placed in the
   middle of a gap of the oracle's singular values, so the integer decision is not a
   rounding tie; the binary64 path must then keep the same number of directions.
@@ -31,9 +31,9 @@ def mor():
     return m
 
 
-def _build_both(mor, sd, p, ranks=None):
+def _build_both(mor, sd, p, ranks=None, mixed_rtol=1e-9):
     out = {}
-    for prec, rt in (("fp64", 1e-11), ("mixed", 1e-9)):
+    for prec, rt in (("fp64", 1e-11), ("mixed", mixed_rtol)):
         kw = dict(rank=int(p["rank"]) if p["rank"] else 1, oversample=p["oversample"],
                   seed=p["seed"], precision=prec, cg_rtol=rt)
         if ranks is not None:
@@ -47,7 +47,20 @@ def _build_both(mor, sd, p, ranks=None):
     return out
 
 
+def _a_orthonormal(V, A):
+    lam, W = np.linalg.eigh(V.T @ (A @ V))
+    keep = lam > 1e-12 * lam.max()
+    return (V @ W[:, keep]) / np.sqrt(lam[keep])
+
+
 def _check_sampled(mesh, kappa, owner, p, sd, out, subs, rank_of):
+    """Index sets bit-exact; singular values within tol * sigma_1; and the oracle's
+    leading basis [q_0, R_i^{-1} U_m'] inside the span of the GPU's Q_i.  m' <= m is the
+    index of the widest relative gap (sigma_m' - sigma_m'+1) / sigma_1 among the first m:
+    by Wedin's theorem the sketched m'-space moves by at most tol / gap', and the GPU's
+    m-space contains its m'-space, so the containment residual has that bound too (a gap
+    as narrow as 1e-4 at m itself, which high-contrast subdomains show, would make the
+    bound on the whole m-space vacuous)."""
     adj = osub.node_adjacency(mesh.tets, mesh.n_nodes)
     for i in subs:
         s = osub.subdomain_sets(mesh, owner, i, p["r_hops"], adj)
@@ -56,8 +69,10 @@ def _check_sampled(mesh, kappa, owner, p, sd, out, subs, rank_of):
         ob = obasis.local_basis(mesh, kappa, s, rank_of(i), p["oversample"], p["seed"])
         m = rank_of(i)
         ref = ob["sigma"]
-        gap = (ref[m - 1] - ref[m]) / ref[0]
+        gaps = (ref[:m] - ref[1:m + 1]) / ref[0]
+        mp = int(np.argmax(gaps)) + 1
         A = ob["A_PP"]
+        Vo = _a_orthonormal(ob["V"][:, :mp + 1], A)
         for prec, tol in (("fp64", 1e-9), ("mixed", 1e-7)):
             b = out[prec][0]
             sig = b.sigma()[i]
@@ -65,11 +80,11 @@ def _check_sampled(mesh, kappa, owner, p, sd, out, subs, rank_of):
             assert np.max(np.abs(sig[:n] - ref[:n])) <= tol * ref[0], (i, prec)
             assert np.all(sig[n:] == 0.0)
             Qg = b.Q(i)[:, :b.kept[i]]
-            Qo = ob["Q"]
-            assert Qg.shape[1] == Qo.shape[1], (i, prec)
-            R = Qg - Qo @ (Qo.T @ (A @ Qg))
+            assert Qg.shape[1] == ob["Q"].shape[1], (i, prec)
+            assert np.allclose(Qg.T @ (A @ Qg), np.eye(Qg.shape[1]), atol=1e-8)
+            R = Vo - Qg @ (Qg.T @ (A @ Vo))
             sin_max = np.sqrt(max(0.0, np.linalg.eigvalsh(R.T @ (A @ R)).max()))
-            assert sin_max <= tol / min(1.0, gap), (i, prec, sin_max, gap)
+            assert sin_max <= tol / gaps[mp - 1], (i, prec, mp, sin_max, gaps[mp - 1])
 
 
 def _check_batch(mor, sd, out):
@@ -113,7 +128,11 @@ def test_high_contrast_spheres(mor):
     gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
     sd = mor.Subdomains(gm, owner, p["r_hops"])
     assert sd.n_sub == 512
-    out = _build_both(mor, sd, p)
+    # a residual tolerance bounds the energy error of a local solve by about
+    # rtol * sqrt(cond(A_II)); with k = 1e4 inclusions cond(A_II) ~ 1e7, so the mixed
+    # path needs cg_rtol 1e-11 (not 1e-9) for 1e-6 relative energy.  Columns that reach
+    # the rounding level of the binary64 residual first stop there.
+    out = _build_both(mor, sd, p, mixed_rtol=1e-11)
     _check_sampled(mesh, kappa, owner, p, sd, out, [0], lambda i: p["rank"])
     _check_batch(mor, sd, out)
 
