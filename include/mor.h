@@ -127,11 +127,17 @@ typedef struct {
                           V^T A_ii V below tau * largest                                */
   double orth_tol;     /* Gram orthonormalisation: drop directions below
                           orth_tol * largest Gram eigenvalue                             */
+  int32_t coarse_rows; /* local preconditioner: > 0 adds a coarse level to Jacobi,
+                          M^{-1} = D^{-1} + Z E^{-1} Z^T with Z the indicators of
+                          spatial aggregates of about coarse_rows rows (runs of the
+                          Morton-ordered rows of a subdomain, at most 256 per
+                          subdomain) and E = Z^T A Z inverted per subdomain; 0: Jacobi
+                          only.  Changes iteration counts, not the solutions.         */
 } mor_basis_opts;
 
 /* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
  * max_iter 20000, replace_every 40, normwise 1, drift_restart 1.5, sketch_rtol 0,
- * tau 1e-12, orth_tol 1e-14). */
+ * tau 1e-12, orth_tol 1e-14, coarse_rows 100). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 
 /* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (24)):
@@ -242,14 +248,17 @@ int mor_energy_norm(const mor_subdomains* sd, const double* u1_dev, const double
 int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts,
                          int32_t sub, double* out, void* stream);
 
-/* Kernel timing for the roofline: when enabled, the three kernels of every local CG
+/* Kernel timing for the roofline: when enabled, the four kernels of every local CG
  * step of mor_build_bases are bracketed by CUDA events on the launching stream.
  * mor_profile_query fills out[host, 4] = {launches, total milliseconds, algorithmic
  * bytes moved, 0} accumulated since the last reset for `family` = 2 * kind + wide,
  * kind 0 = sparse product q = A p with the p.q column sums, 1 = x/r update with the
- * r.r and r.z sums, 2 = p update; wide 0 = binary32, 1 = binary64.  Algorithmic
- * bytes count every stored nonzero (value + column index) and every vector block
- * element the kernel must read or write once.  Process-wide state, not thread-safe. */
+ * r.r and fine r.z sums and the restriction Z^T r, 2 = p update with the
+ * prolongation and the p.r sums, 3 = coarse solve E^{-1} Z^T r; wide 0 = binary32,
+ * 1 = binary64 (families 0..7).  Algorithmic bytes count every stored nonzero (value
+ * + column index) and every vector block element the kernel must read or write once
+ * (the coarse kernel: its E^{-1} blocks once per 16-column chunk).  Process-wide
+ * state, not thread-safe. */
 int mor_profile_enable(int32_t on);
 int mor_profile_reset(void);
 int mor_profile_query(int32_t family, double* out);

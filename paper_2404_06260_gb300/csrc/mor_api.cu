@@ -89,6 +89,7 @@ int upload_tiles(Allocs& A, const HostTiles& h, DTiles& d, cudaStream_t st) {
   TRY(A.upload(&lo, h.lo, st));
   TRY(A.upload(&hi, h.hi, st));
   d.n = (int)h.sd.size();
+  d.n_sd = (int)h.lo.size();
   d.sd = sd;
   d.r0 = r0;
   d.r1 = r1;
@@ -98,32 +99,37 @@ int upload_tiles(Allocs& A, const HostTiles& h, DTiles& d, cudaStream_t st) {
 }
 
 // ---- kernel timing (roofline) ------------------------------------------------------
-// family = 2 * kind + wide (kind 0 sparse product, 1 x/r update, 2 p update)
-constexpr int kFamilies = 6;
+// family = 2 * kind + wide (kind 0 sparse product, 1 x/r update, 2 p update, 3 coarse
+// solve).  The events of one step: before the product, after the product, after the
+// x/r update, after the coarse kernel, after the p update.
+constexpr int kFamilies = 8;
 struct Prof {
   bool on = false;
   double launches[kFamilies] = {}, ms[kFamilies] = {}, bytes[kFamilies] = {};
-  std::vector<std::array<cudaEvent_t, 4>> pool;
+  std::vector<std::array<cudaEvent_t, 5>> pool;
   struct Pending {
     int wide;
-    double bytes[3];
+    double bytes[4];
     size_t ev;
   };
   std::vector<Pending> pending;
   size_t used = 0;
   const cudaEvent_t* take() {
     if (used == pool.size()) {
-      std::array<cudaEvent_t, 4> e;
+      std::array<cudaEvent_t, 5> e;
       for (auto& x : e) cudaEventCreate(&x);
       pool.push_back(e);
     }
     return pool[used++].data();
   }
   void collect() {
+    // event interval of each kind: product [0,1], x/r [1,2], p update [3,4], coarse [2,3]
+    static const int from[4] = {0, 1, 3, 2};
     for (auto& p : pending)
-      for (int kind = 0; kind < 3; ++kind) {
+      for (int kind = 0; kind < 4; ++kind) {
         float t = 0.f;
-        if (cudaEventElapsedTime(&t, pool[p.ev][kind], pool[p.ev][kind + 1]) == cudaSuccess) {
+        int e0 = from[kind];
+        if (cudaEventElapsedTime(&t, pool[p.ev][e0], pool[p.ev][e0 + 1]) == cudaSuccess) {
           int f = 2 * kind + p.wide;
           launches[f] += 1;
           ms[f] += t;
@@ -202,8 +208,16 @@ int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_h
   cudaStream_t st = (cudaStream_t)stream;
   auto h = std::make_unique<mor_subdomains_s>();
   std::string err;
+  // node positions order the rows of each subdomain (Morton order within I and B)
+  std::vector<double> xyz_host;
+  if (mesh->n_nodes > 0) {
+    xyz_host.resize((size_t)mesh->n_nodes * 3);
+    CK(cudaMemcpyAsync(xyz_host.data(), mesh->xyz_dev, xyz_host.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
   int rc = build_host_plan(mesh->n_nodes, mesh->n_tets, mesh->tets, mesh->dirichlet, owner,
-                           r_hops, h->hp, err);
+                           r_hops, xyz_host.empty() ? nullptr : xyz_host.data(), h->hp, err);
   if (rc != MOR_OK) return fail(rc, err);
   const HostPlan& hp = h->hp;
   h->xyz = mesh->xyz_dev;
@@ -310,6 +324,7 @@ int mor_basis_opts_default(mor_basis_opts* o) {
   o->sketch_rtol = 0.0;
   o->tau = 1e-12;
   o->orth_tol = 1e-14;
+  o->coarse_rows = 100;
   return MOR_OK;
 }
 
@@ -357,9 +372,23 @@ struct Build {
     return *h_poll;
   }
 
+  // coarse levels of the two-level preconditioner: [0] A_II (I tiles), [1] H^+ (all P
+  // tiles); cbytes = algorithmic bytes of one coarse kernel launch per set
+  Coarse<float> co32[2];
+  Coarse<double> co64[2];
+  double cbytes[2] = {0, 0};
+  template <typename T>
+  const Coarse<T>& coarse_of(int set) const {
+    if constexpr (sizeof(T) == 4)
+      return co32[set];
+    else
+      return co64[set];
+  }
+
   template <typename T>
   int solve(const DTiles& tl, const Mat& A, const T* dinvT, const double* b64, double* x64,
-            int nc, int which, double rtol) {
+            int nc, int which, double rtol, int set) {
+    const Coarse<T>& co = coarse_of<T>(set);
     // columns [0, ncn) share the block-normwise reference; the load column (forward
     // solve, column k) keeps its own
     const int ncn = o->normwise ? std::min(nc, k) : 0;
@@ -374,8 +403,9 @@ struct Build {
     T* q = (T*)qT;
     T* b = (T*)bT;
     double rtol2 = rtol * rtol;
-    double pb[3] = {0, 0, 0};
+    double pb[4] = {0, 0, 0, 0};
     if (g_prof.on) prof_bytes(tl, A, sizeof(T), pb);
+    pb[3] = cbytes[set] * (double)sizeof(T);
     // one CG per (subdomain, column) in precision T on the full system, with the
     // recursively updated residual replaced by the binary64 residual b - A x64 every
     // replace_every iterations and whenever the recursion reports convergence
@@ -384,7 +414,7 @@ struct Build {
     launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 1, false, rs, st);
     if (poll(rs.active) == 0) return MOR_OK;
     launch_cast<T>(tl, vR64, b, kp, st);
-    launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, ncn, cs, st);
+    launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, ncn, cs, co, st);
     const int check = 8;
     const int every = std::max(check, o->replace_every / check * check);
     int it = 0, nsweep = 0;
@@ -395,9 +425,10 @@ struct Build {
         if (g_prof.on) {
           ev = g_prof.take();
           g_prof.pending.push_back(
-              Prof::Pending{sizeof(T) == 4 ? 0 : 1, {pb[0], pb[1], pb[2]}, g_prof.used - 1});
+              Prof::Pending{sizeof(T) == 4 ? 0 : 1, {pb[0], pb[1], pb[2], pb[3]},
+                            g_prof.used - 1});
         }
-        launch_cg_step<T>(tl, AT, x, r, p, q, dinvT, kp, rtol2, cs, st, ev);
+        launch_cg_step<T>(tl, AT, x, r, p, q, dinvT, kp, rtol2, cs, co, st, ev);
       }
       it += chunk;
       int act = poll(cs.active);
@@ -433,7 +464,7 @@ struct Build {
           if (ract > 0) not_conv += ract;
           break;
         }
-        launch_cg_replace<T>(tl, vR64, r, p, dinvT, kp, o->drift_restart, cs, rs, st);
+        launch_cg_replace<T>(tl, vR64, r, p, dinvT, kp, o->drift_restart, cs, rs, co, st);
       }
     }
     iters[which] += it;
@@ -441,14 +472,15 @@ struct Build {
     return MOR_OK;
   }
 
-  // algorithmic bytes of the three kernels of one CG step on the rows of tl:
+  // algorithmic bytes of the kernels of one CG step on the rows of tl:
   // sparse product = every stored nonzero (value + column index) once + read p and
   // write q once; x/r update = read x, r, p, q and write x, r (+ the diagonal);
-  // p update = read r, p and write p (+ the diagonal)
+  // p update = read r, p and write p (+ the diagonal); coarse kernel = its E^{-1}
+  // blocks once per column chunk (set in cbytes)
   std::vector<double> nnz_by_mat;
   const Mat* mats[8] = {};
   double rows_of(const DTiles& tl) const;
-  void prof_bytes(const DTiles& tl, const Mat& A, size_t tsz, double out[3]) {
+  void prof_bytes(const DTiles& tl, const Mat& A, size_t tsz, double out[4]) {
     double nnz = 0;
     for (int i = 0; i < 8; ++i)
       if (mats[i] == &A) nnz = nnz_by_mat[i];
@@ -606,6 +638,73 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   CK(cudaStreamSynchronize(st));
   if (h_err) return fail(MOR_ERR_BAD_MESH, "mor_build_bases: element with non-positive volume");
 
+  // ---- coarse level of the local preconditioner (set 0: A_II, set 1: H^+) ----
+  if (o.coarse_rows > 0) {
+    AggPlan ap;
+    build_aggregates(hp, o.coarse_rows, kMaxAgg, ap);
+    if (ap.max_slots > kMaxSlots)
+      return fail(MOR_ERR_ARG, "mor_build_bases: too many aggregates meet one row tile");
+    const int64_t n_agg = ap.aoff[n_sd];
+    int32_t *aloc, *aoff;
+    TRY(M.upload(&aloc, ap.aloc, st));
+    TRY(M.upload(&aoff, ap.aoff, st));
+    const size_t tsz_c = B.mixed ? sizeof(float) : sizeof(double);
+    void* yc;
+    TRY(M.alloc((unsigned char**)&yc, (size_t)n_agg * kp * tsz_c, true, st));
+    int* d_bad;
+    TRY(M.alloc(&d_bad, 1, true, st));
+    const int nchunk = (kp + 15) / 16;
+    for (int set = 0; set < 2; ++set) {
+      const DTiles& tl = set == 0 ? S.tP_I : S.tP_all;
+      const Mat& Am = set == 0 ? A_II : Hp;
+      int32_t *nca, *tfirst, *tcount;
+      int64_t *toff, *eoff;
+      TRY(M.upload(&nca, ap.nca[set], st));
+      TRY(M.upload(&tfirst, ap.tfirst[set], st));
+      TRY(M.upload(&tcount, ap.tcount[set], st));
+      TRY(M.upload(&toff, ap.toff[set], st));
+      TRY(M.upload(&eoff, ap.eoff[set], st));
+      const int64_t ne = ap.eoff[set][n_sd];
+      double* E;
+      TRY(M.alloc(&E, std::max<int64_t>(ne, 1), true, st));
+      void *einv, *cpart;
+      TRY(M.alloc((unsigned char**)&einv, (size_t)std::max<int64_t>(ne, 1) * tsz_c, true, st));
+      TRY(M.alloc((unsigned char**)&cpart, (size_t)std::max<int64_t>(ap.toff[set].back(), 1) *
+                                               kp * tsz_c, true, st));
+      launch_coarse_matrix(tl, Am.e64(), aloc, nca, eoff, E, st);
+      if (B.mixed)
+        launch_coarse_invert<float>(n_sd, nca, eoff, E, (float*)einv, d_bad, st);
+      else
+        launch_coarse_invert<double>(n_sd, nca, eoff, E, (double*)einv, d_bad, st);
+      B.cbytes[set] = (double)ne * nchunk;
+      auto fill = [&](auto& c, auto* ei, auto* cp, auto* y) {
+        c.aloc = aloc;
+        c.aoff = aoff;
+        c.nca = nca;
+        c.tfirst = tfirst;
+        c.tcount = tcount;
+        c.toff = toff;
+        c.eoff = eoff;
+        c.einv = ei;
+        c.cpart = cp;
+        c.yc = y;
+      };
+      if (B.mixed)
+        fill(B.co32[set], (const float*)einv, (float*)cpart, (float*)yc);
+      else
+        fill(B.co64[set], (const double*)einv, (double*)cpart, (double*)yc);
+    }
+    int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_bad)  // an aggregate matrix that is not SPD: keep the Jacobi preconditioner
+      for (int set = 0; set < 2; ++set) {
+        B.co32[set] = Coarse<float>();
+        B.co64[set] = Coarse<double>();
+        B.cbytes[set] = 0;
+      }
+  }
+
   // ---- solver workspace ----
   size_t tsz = B.mixed ? sizeof(float) : sizeof(double);
   double *vS, *vG, *vF, *vX;
@@ -633,6 +732,9 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.alloc(&B.cs.alpha, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.beta, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.rr, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.rzf, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.gam, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.pr, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.done, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.part1, (size_t)mt * kp, true, st));
   TRY(M.alloc(&B.cs.part2, (size_t)mt * kp, true, st));
@@ -681,8 +783,10 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
 
   auto solve = [&](const DTiles& tl, const Mat& A, bool isA, const double* b64, double* x64,
                    int nc, int which, double rtol) -> int {
-    if (B.mixed) return B.solve<float>(tl, A, isA ? dA32 : dH32, b64, x64, nc, which, rtol);
-    return B.solve<double>(tl, A, isA ? dA64 : dH64, b64, x64, nc, which, rtol);
+    const int set = isA ? 0 : 1;
+    if (B.mixed)
+      return B.solve<float>(tl, A, isA ? dA32 : dH32, b64, x64, nc, which, rtol, set);
+    return B.solve<double>(tl, A, isA ? dA64 : dH64, b64, x64, nc, which, rtol, set);
   };
   const double rt = o.cg_rtol;
   const double rt_sketch = o.sketch_rtol > 0.0 ? o.sketch_rtol : o.cg_rtol;
@@ -968,8 +1072,19 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, i
   launch_sketch_rhs(row0, n_rows, sd->p_sd, sd->incP_ptr,
                     sd->incP_tet, sd->incP_code, lrow, k, opts->seed, res, k, st, nullptr);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(out, res + row0 * k, n_rows * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<double> tmp((size_t)n_rows * k);
+  CK(cudaMemcpyAsync(tmp.data(), res + row0 * k, tmp.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  // P rows are in Morton order within I and B; report I then B in ascending node order
+  const SubSets& ss = hp.sets[sub];
+  const int64_t nI = (int64_t)ss.I.size();
+  for (int64_t l = 0; l < n_rows; ++l) {
+    int32_t v = hp.p_node[row0 + l];
+    int64_t dst = l < nI ? std::lower_bound(ss.I.begin(), ss.I.end(), v) - ss.I.begin()
+                         : nI + (std::lower_bound(ss.B.begin(), ss.B.end(), v) - ss.B.begin());
+    std::copy(tmp.begin() + l * k, tmp.begin() + (l + 1) * k, out + dst * k);
+  }
   return MOR_OK;
 }
 

@@ -14,6 +14,7 @@ __host__ __device__ __forceinline__ int64_t ell_at(int64_t r, int j, int W) {
 
 struct DTiles {
   int n = 0;
+  int n_sd = 0;                 // subdomains (lo/hi length)
   const int32_t* sd = nullptr;
   const int32_t* r0 = nullptr;
   const int32_t* r1 = nullptr;

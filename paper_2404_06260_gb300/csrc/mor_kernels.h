@@ -70,11 +70,36 @@ void launch_iface_vals(int64_t n_e, const int32_t* unode, const int32_t* vnode,
 struct CgState {
   double *rz, *bb, *alpha, *beta;  // n_sd x kp
   double* rr;                       // n_sd x kp: recursive ||r||^2 after the last update
+  double* rzf;                      // n_sd x kp: r^T D^{-1} r (the fine part of r^T M^{-1} r)
+  double* gam;                      // n_sd x kp: p = gam z + beta p in the p update
+  double* pr;                       // n_sd x kp: p.r after the p update (the step length
+                                    // is the exact line search alpha = p.r / p.Ap)
   int* done;                        // n_sd x kp
   double *part1, *part2;            // n_tiles x kp
   int* counter;                     // n_sd
   int* iters;                       // n_sd
   int* active;                      // n_sd: active columns after the last update
+};
+
+// Coarse level of the two-level additive preconditioner M^{-1} = D^{-1} + Z E^{-1} Z^T
+// of the local solves.  Z has one indicator column per aggregate: a contiguous run of
+// rows of one subdomain (rows are in Morton order, so a run is a spatial box);
+// E = Z^T A Z per subdomain, inverted once per matrix.  With aloc = null the
+// preconditioner is D^{-1} alone.
+constexpr int kMaxSlots = 32;  // aggregates meeting one row tile (host-enforced)
+constexpr int kMaxAgg = 256;   // aggregates per subdomain and matrix (host-enforced)
+template <typename T>
+struct Coarse {
+  const int32_t* aloc = nullptr;    // per P row: aggregate index within its subdomain
+  const int32_t* aoff = nullptr;    // per subdomain: first global aggregate id
+  const int32_t* nca = nullptr;     // per subdomain: aggregates of this matrix (<= kMaxAgg)
+  const int32_t* tfirst = nullptr;  // per global aggregate: first tile holding its rows
+  const int32_t* tcount = nullptr;  // per global aggregate: tiles holding its rows
+  const int64_t* toff = nullptr;    // per tile: first row of its partials (n_tiles + 1)
+  const int64_t* eoff = nullptr;    // per subdomain: offset of its nca x nca block
+  const T* einv = nullptr;          // E^{-1} blocks, symmetric, row-major
+  T* cpart = nullptr;               // toff[n_tiles] x kp restriction partials
+  T* yc = nullptr;                  // global aggregates x kp: E^{-1} Z^T r
 };
 
 template <typename T>
@@ -90,18 +115,21 @@ template <typename T>
 void launch_spmm(const DTiles& tiles, const EllView<T>& A, const T* X, T* Y, int kp,
                  cudaStream_t st);
 
-// Jacobi-preconditioned CG, independent per (subdomain, column), one step = 3 kernels.
-// columns c < ncn of a subdomain measure convergence against the largest ||b_c|| among
-// them (block-normwise); the others against their own ||b_c||
+// Preconditioned CG (Jacobi, or two-level with a Coarse level), independent per
+// (subdomain, column); one step = 4 kernels (sparse product with p.q, x/r update with
+// the fine r.z and the restriction, coarse solve with beta, p update).  Columns
+// c < ncn of a subdomain measure convergence against the largest ||b_c|| among them
+// (block-normwise); the others against their own ||b_c||.
 template <typename T>
 void launch_cg_init(const DTiles& tiles, const T* b, T* x, T* r, T* p, const T* dinv,
-                    int kp, int nc, int ncn, const CgState& s, cudaStream_t st);
-// ev (null or 4 events) is recorded before the sparse product and after each of the
-// three kernels of the step.
+                    int kp, int nc, int ncn, const CgState& s, const Coarse<T>& co,
+                    cudaStream_t st);
+// ev (null or 5 events) is recorded before the sparse product and after each of the
+// four kernels of the step.
 template <typename T>
 void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, T* q,
-                    const T* dinv, int kp, double tol2, const CgState& s, cudaStream_t st,
-                    const cudaEvent_t* ev = nullptr);
+                    const T* dinv, int kp, double tol2, const CgState& s,
+                    const Coarse<T>& co, cudaStream_t st, const cudaEvent_t* ev = nullptr);
 void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st);
 
 // binary64 residual: r64 = b64 - A64 x64 with per-column norms; scale = 1/||r64|| for
@@ -127,11 +155,22 @@ void launch_residual64(const DTiles& tiles, const EllView<double>& A, const doub
 void launch_zero_rows(const DTiles& tiles, double* x, int kp, cudaStream_t st);
 // residual replacement of the CG recursion: rT = (T) r64, rz recomputed, done flags from
 // the binary64 convergence test of launch_residual64 (scale == 0 means converged);
-// reopened columns restart with pT = D^{-1} rT
+// reopened columns restart with pT = M^{-1} rT
 template <typename T>
 void launch_cg_replace(const DTiles& tiles, const double* r64, T* rT, T* pT, const T* dinv,
                        int kp, double drift, const CgState& s, const RefineState& rs,
-                       cudaStream_t st);
+                       const Coarse<T>& co, cudaStream_t st);
+
+// ---------------- coarse level setup (mor_coarse.cu) ----------------
+// E[sd][a][b] += A[i][j] over the stored entries of the rows of tiles, a = aloc[i],
+// b = aloc[j] (entries with a or b >= nca[sd] are skipped); E zeroed by the caller.
+void launch_coarse_matrix(const DTiles& tiles, const EllView<double>& A, const int32_t* aloc,
+                          const int32_t* nca, const int64_t* eoff, double* E, cudaStream_t st);
+// In-place Gauss-Jordan inverse of every SPD block E[sd] (binary64, no pivoting), then
+// einv = (E^{-1} + E^{-T}) / 2 in T.  bad[0] counts blocks with a non-positive pivot.
+template <typename T>
+void launch_coarse_invert(int n_sd, const int32_t* nca, const int64_t* eoff, double* E,
+                          T* einv, int* bad, cudaStream_t st);
 // x64 += xT, xT = 0
 template <typename T>
 void launch_accum_reset(const DTiles& tiles, T* xT, double* x64, int kp, cudaStream_t st);

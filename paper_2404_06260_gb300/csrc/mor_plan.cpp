@@ -152,11 +152,62 @@ void pack_ell(const std::vector<SubOut>& outs, bool plus, const std::vector<int6
   }
 }
 
+// spread the low 10 bits of v to every third bit
+uint32_t spread3(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// I and B in Morton order of the node positions quantised to 1024 cells per axis of
+// the bounding box of I u B (ties by node id); codes in the same order
+void morton_order(const double* xyz, const std::vector<int32_t>& I,
+                  const std::vector<int32_t>& B, std::vector<int32_t>& Ip,
+                  std::vector<int32_t>& Bp, std::vector<uint32_t>& code) {
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  bool first = true;
+  if (xyz)
+    for (const auto* seg : {&I, &B})
+      for (int32_t v : *seg)
+        for (int a = 0; a < 3; ++a) {
+          double x = xyz[3 * (int64_t)v + a];
+          if (first || x < lo[a]) lo[a] = x;
+          if (first || x > hi[a]) hi[a] = x;
+          if (a == 2) first = false;
+        }
+  auto key = [&](int32_t v) -> uint32_t {
+    if (!xyz) return 0u;
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+      double w = hi[a] - lo[a];
+      double t = w > 0.0 ? (xyz[3 * (int64_t)v + a] - lo[a]) / w * 1024.0 : 0.0;
+      q[a] = (uint32_t)std::min(1023.0, std::max(0.0, std::floor(t)));
+    }
+    return (spread3(q[2]) << 2) | (spread3(q[1]) << 1) | spread3(q[0]);
+  };
+  code.clear();
+  for (int s = 0; s < 2; ++s) {
+    const std::vector<int32_t>& src = s == 0 ? I : B;
+    std::vector<std::pair<uint32_t, int32_t>> kv(src.size());
+    for (size_t l = 0; l < src.size(); ++l) kv[l] = {key(src[l]), src[l]};
+    std::sort(kv.begin(), kv.end());
+    std::vector<int32_t>& dst = s == 0 ? Ip : Bp;
+    dst.resize(src.size());
+    for (size_t l = 0; l < kv.size(); ++l) {
+      dst[l] = kv[l].second;
+      code.push_back(kv[l].first);
+    }
+  }
+}
+
 }  // namespace
 
 int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
                     const uint8_t* dirichlet, const int32_t* owner, int32_t r_hops,
-                    HostPlan& hp, std::string& err) {
+                    const double* xyz, HostPlan& hp, std::string& err) {
   if (n_nodes <= 0 || n_tets <= 0 || !tets || !dirichlet || !owner) {
     err = "mor_build_subdomains: empty mesh or null array";
     return MOR_ERR_ARG;
@@ -290,14 +341,15 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     for (size_t w = 0; w < ss.omega.size(); ++w) S.wloc[ss.omega[w]] = (int32_t)w;
     for (int32_t v : P[i])
       if (!dirichlet[v]) ss.owned.push_back(v);
-    // plus-local numbering: I then B
-    for (size_t l = 0; l < ss.I.size(); ++l) {
-      S.loc_mark[ss.I[l]] = st;
-      S.loc[ss.I[l]] = (int32_t)l;
+    // plus-local numbering: I then B, each in Morton order
+    morton_order(xyz, ss.I, ss.B, ss.Ip, ss.Bp, ss.pcode);
+    for (size_t l = 0; l < ss.Ip.size(); ++l) {
+      S.loc_mark[ss.Ip[l]] = st;
+      S.loc[ss.Ip[l]] = (int32_t)l;
     }
-    for (size_t l = 0; l < ss.B.size(); ++l) {
-      S.loc_mark[ss.B[l]] = st;
-      S.loc[ss.B[l]] = (int32_t)(ss.I.size() + l);
+    for (size_t l = 0; l < ss.Bp.size(); ++l) {
+      S.loc_mark[ss.Bp[l]] = st;
+      S.loc[ss.Bp[l]] = (int32_t)(ss.Ip.size() + l);
     }
     so.w2p_local.resize(ss.omega.size());
     for (size_t w = 0; w < ss.omega.size(); ++w) {
@@ -311,8 +363,8 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     so.o2w_local.resize(ss.owned.size());
     for (size_t o = 0; o < ss.owned.size(); ++o) so.o2w_local[o] = S.wloc[ss.owned[o]];
     if (so.err.empty()) {
-      std::vector<int32_t> prow(ss.I);
-      prow.insert(prow.end(), ss.B.begin(), ss.B.end());
+      std::vector<int32_t> prow(ss.Ip);
+      prow.insert(prow.end(), ss.Bp.begin(), ss.Bp.end());
       build_rows(prow, tets, n2t_ptr, n2t, S.tplus, S.loc_mark, S.loc, st, so.P);
       build_rows(ss.omega, tets, n2t_ptr, n2t, S.tomega, S.wmark, S.wloc, st, so.W);
     }
@@ -350,6 +402,7 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
   hp.p_node.resize(hp.nP);
   hp.p_sd.resize(hp.nP);
   hp.p_isB.resize(hp.nP);
+  hp.p_code.resize(hp.nP);
   hp.w_node.resize(hp.nW);
   hp.w_sd.resize(hp.nW);
   hp.w2p.resize(hp.nW);
@@ -361,16 +414,17 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
   for (int i = 0; i < n_sd; ++i) {
     const SubSets& ss = hp.sets[i];
     int64_t p0 = hp.Poff[i], w0 = hp.Woff[i], o0 = hp.Ooff[i];
-    for (size_t l = 0; l < ss.I.size(); ++l) {
-      hp.p_node[p0 + l] = ss.I[l];
+    for (size_t l = 0; l < ss.Ip.size(); ++l) {
+      hp.p_node[p0 + l] = ss.Ip[l];
       hp.p_sd[p0 + l] = i;
       hp.p_isB[p0 + l] = 0;
     }
-    for (size_t l = 0; l < ss.B.size(); ++l) {
-      hp.p_node[p0 + ss.I.size() + l] = ss.B[l];
-      hp.p_sd[p0 + ss.I.size() + l] = i;
-      hp.p_isB[p0 + ss.I.size() + l] = 1;
+    for (size_t l = 0; l < ss.Bp.size(); ++l) {
+      hp.p_node[p0 + ss.Ip.size() + l] = ss.Bp[l];
+      hp.p_sd[p0 + ss.Ip.size() + l] = i;
+      hp.p_isB[p0 + ss.Ip.size() + l] = 1;
     }
+    for (size_t l = 0; l < ss.pcode.size(); ++l) hp.p_code[p0 + l] = ss.pcode[l];
     for (size_t w = 0; w < ss.omega.size(); ++w) {
       hp.w_node[w0 + w] = ss.omega[w];
       hp.w_sd[w0 + w] = i;
@@ -458,6 +512,114 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
   }
   if (!ents.empty()) hp.pair_ptr.push_back((int64_t)ents.size());
   return MOR_OK;
+}
+
+namespace {
+
+constexpr int kMinAggRows = 8;
+
+// leading equal bits (of 30) of two Morton codes
+int lead_equal(uint32_t a, uint32_t b) {
+  uint32_t x = (a ^ b) & 0x3FFFFFFFu;
+  int n = 30;
+  while (x) {
+    x >>= 1;
+    --n;
+  }
+  return n;
+}
+
+// prefix length b whose run count is closest (in ratio) to want, from the histogram of
+// leading equal bits between consecutive codes (a boundary at level b where lead < b)
+int pick_bits(const uint32_t* code, int n, double want) {
+  if (n <= 1 || want <= 1.0) return 0;
+  int hist[31] = {0};
+  for (int l = 1; l < n; ++l) ++hist[lead_equal(code[l - 1], code[l])];
+  int best = 0;
+  double best_err = 1e300, runs = 1.0;
+  for (int b = 0; b <= 30; ++b) {
+    if (b > 0) runs += hist[b - 1];
+    double err = std::fabs(std::log(runs / want));
+    if (err < best_err) {
+      best_err = err;
+      best = b;
+    }
+  }
+  return best;
+}
+
+// run starts of equal (code >> (30 - b)), short runs joined to the previous run (a short
+// first run to the next one)
+void cut_runs(const uint32_t* code, int n, int b, std::vector<int>& starts) {
+  starts.clear();
+  if (n <= 0) return;
+  const int sh = 30 - b;
+  std::vector<int> raw{0};
+  for (int l = 1; l < n; ++l)
+    if (b > 0 && (code[l] >> sh) != (code[l - 1] >> sh)) raw.push_back(l);
+  for (size_t r = 0; r < raw.size(); ++r) {
+    int e = r + 1 < raw.size() ? raw[r + 1] : n;
+    if (starts.empty() || e - raw[r] >= kMinAggRows) starts.push_back(raw[r]);
+  }
+  if (starts.size() >= 2 && starts[1] - starts[0] < kMinAggRows) starts.erase(starts.begin() + 1);
+}
+
+}  // namespace
+
+void build_aggregates(const HostPlan& hp, int target_rows, int max_agg, AggPlan& ap) {
+  const int n_sd = hp.n_sd;
+  ap = AggPlan();
+  ap.aloc.assign(hp.nP, 0);
+  ap.aoff.assign(n_sd + 1, 0);
+  ap.nca[0].assign(n_sd, 0);
+  ap.nca[1].assign(n_sd, 0);
+  std::vector<int> sI, sB;
+  for (int i = 0; i < n_sd; ++i) {
+    const int nI = hp.nI[i], nB = hp.nB[i];
+    const uint32_t* cI = hp.p_code.data() + hp.Poff[i];
+    const uint32_t* cB = cI + nI;
+    double t = std::max(1, target_rows);
+    for (int attempt = 0; attempt < 64; ++attempt) {
+      cut_runs(cI, nI, pick_bits(cI, nI, nI / t), sI);
+      cut_runs(cB, nB, pick_bits(cB, nB, nB / t), sB);
+      if ((int)(sI.size() + sB.size()) <= max_agg) break;
+      t *= 1.25;
+    }
+    int32_t* al = ap.aloc.data() + hp.Poff[i];
+    for (size_t r = 0; r < sI.size(); ++r) {
+      int e = r + 1 < sI.size() ? sI[r + 1] : nI;
+      for (int l = sI[r]; l < e; ++l) al[l] = (int32_t)r;
+    }
+    for (size_t r = 0; r < sB.size(); ++r) {
+      int e = r + 1 < sB.size() ? sB[r + 1] : nB;
+      for (int l = sB[r]; l < e; ++l) al[nI + l] = (int32_t)(sI.size() + r);
+    }
+    ap.nca[0][i] = (int32_t)sI.size();
+    ap.nca[1][i] = (int32_t)(sI.size() + sB.size());
+    ap.aoff[i + 1] = ap.aoff[i] + ap.nca[1][i];
+  }
+  const int64_t n_agg = ap.aoff[n_sd];
+  for (int set = 0; set < 2; ++set) {
+    const HostTiles& T = set == 0 ? hp.tP_I : hp.tP_all;
+    const size_t nt = T.sd.size();
+    ap.toff[set].assign(nt + 1, 0);
+    ap.tfirst[set].assign(n_agg, 0);
+    ap.tcount[set].assign(n_agg, 0);
+    for (size_t t = 0; t < nt; ++t) {
+      const int sd = T.sd[t];
+      const int a0 = ap.aloc[T.r0[t]], a1 = ap.aloc[T.r1[t] - 1];
+      const int ns = a1 - a0 + 1;
+      ap.max_slots = std::max(ap.max_slots, ns);
+      ap.toff[set][t + 1] = ap.toff[set][t] + ns;
+      for (int a = a0; a <= a1; ++a) {
+        int64_t ga = ap.aoff[sd] + a;
+        if (ap.tcount[set][ga]++ == 0) ap.tfirst[set][ga] = (int32_t)t;
+      }
+    }
+    ap.eoff[set].assign(n_sd + 1, 0);
+    for (int i = 0; i < n_sd; ++i)
+      ap.eoff[set][i + 1] = ap.eoff[set][i] + (int64_t)ap.nca[set][i] * ap.nca[set][i];
+  }
 }
 
 }  // namespace mor

@@ -28,7 +28,12 @@ struct HostTiles {
 };
 
 struct SubSets {
-  std::vector<int32_t> I, B, omega, owned, plus_tets, omega_tets;
+  std::vector<int32_t> I, B, omega, owned, plus_tets, omega_tets;  // ascending node ids
+  // the rows of I and B in P-space order: each sorted by the Morton code of the node
+  // position in the bounding box of T_i^+ (codes in pcode, I rows then B rows), so a
+  // box of any dyadic size holds a contiguous run of rows
+  std::vector<int32_t> Ip, Bp;
+  std::vector<uint32_t> pcode;
 };
 
 struct HostPlan {
@@ -44,6 +49,7 @@ struct HostPlan {
   int64_t nP = 0, nW = 0, nO = 0;
   std::vector<int32_t> p_node, p_sd, w_node, w_sd, w2p, w2o, o2w, o_node, o_sd;
   std::vector<uint8_t> p_isB;
+  std::vector<uint32_t> p_code;  // 30-bit Morton code of each P row (see SubSets)
   // patterns on T_i^+ (P space) and omega_i (W space); columns are space indices
   HostEll pat_P, pat_W;
   // assembly incidence, CSR over rows: element id and code
@@ -62,9 +68,28 @@ struct HostPlan {
   std::vector<int32_t> n2t;
 };
 
+// Aggregates of the coarse level of the local preconditioner: the I rows and the B rows
+// of each subdomain (Morton order) are cut into runs of equal Morton prefix, the prefix
+// length per segment chosen for about target_rows rows a run; runs shorter than 8 rows
+// join a neighbouring run of their segment; at most max_agg runs per subdomain (coarser
+// prefixes otherwise).  I aggregates are numbered first.  Set 0 = the I tiles (A_II
+// solves, I aggregates), set 1 = all P tiles (H^+ solves, all aggregates).
+struct AggPlan {
+  std::vector<int32_t> aloc;        // per P row: aggregate within its subdomain
+  std::vector<int32_t> aoff;        // n_sd + 1: global id of the first aggregate
+  std::vector<int32_t> nca[2];      // per subdomain: aggregates of set 0 / 1
+  std::vector<int64_t> toff[2];     // per tile + 1: partial rows of the tile
+  std::vector<int32_t> tfirst[2], tcount[2];  // per global aggregate
+  std::vector<int64_t> eoff[2];     // n_sd + 1: offsets of the nca x nca blocks
+  int max_slots = 0;                // most aggregates meeting one tile
+};
+void build_aggregates(const HostPlan& hp, int target_rows, int max_agg, AggPlan& ap);
+
 // Returns 0 or a MOR_ERR_* code (err receives a message).
+// xyz (host, n_nodes x 3) orders the rows of each subdomain; with xyz = nullptr they
+// stay in ascending node order (all codes 0).
 int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
                     const uint8_t* dirichlet, const int32_t* owner, int32_t r_hops,
-                    HostPlan& hp, std::string& err);
+                    const double* xyz, HostPlan& hp, std::string& err);
 
 }  // namespace mor

@@ -69,7 +69,7 @@ __device__ __forceinline__ Smem<T> smem_layout(const Geo& g, int kp, int W) {
   return s;
 }
 template <typename T>
-size_t smem_bytes(int nch, int rb, int kp, int W) {
+__host__ __device__ __forceinline__ size_t smem_bytes(int nch, int rb, int kp, int W) {
   size_t nth = (size_t)nch * rb;
   return align16(16 * nth) + align16(sizeof(double) * (nth + 2 * kp)) +
          align16(sizeof(int32_t) * (size_t)kTileRows * W) + sizeof(T) * (size_t)kTileRows * W;
@@ -291,9 +291,11 @@ __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
     int i = sd * kp + c;
     double a = 0.0;
     if (!s.done[i]) {
+      // exact line search along p: alpha = p.r / p.Ap (equals r.z / p.Ap in exact CG,
+      // and stays a descent step after a residual replacement kept p)
       double pq = sm.sums[c];
       if (pq > 0.0)
-        a = s.rz[i] / pq;
+        a = s.pr[i] / pq;
       else
         s.done[i] = 1;  // breakdown (p = 0 or indefinite): stop this column
     }
@@ -384,14 +386,73 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Restriction r_c = Z^T r on a row tile: aggregates are contiguous runs of rows, so the
+// rows of one thread (increasing) change aggregate rarely; each thread keeps a running
+// sum and adds it to the tile's slot (aggregate - aggregate of the first row) in shared
+// memory when its aggregate changes.  The tile's slots then go to cpart in order.
 template <typename T>
-__global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r, T* p,
-                          const T* __restrict__ dinv, int kp, int nc, int ncn, CgState s) {
+__device__ __forceinline__ T* slot_smem(const Geo& g, int kp) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  return reinterpret_cast<T*>(raw + align16(smem_bytes<T>(g.nch, g.rb, kp, 0)));
+}
+size_t slot_smem_bytes(size_t base, int kp, size_t tsz) {
+  return align16(base) + (size_t)kMaxSlots * kp * tsz;
+}
+
+template <typename T>
+struct RestrictAcc {
+  static constexpr int N = Pack<T>::N;
+  int cur = -1;
+  T acc[N];
+  __device__ __forceinline__ void flush(T* cs, int kp, int tx) {
+    if (cur >= 0)
+#pragma unroll
+      for (int e = 0; e < N; ++e) atomicAdd(&cs[cur * kp + tx * N + e], acc[e]);
+  }
+  __device__ __forceinline__ void add(T* cs, int kp, int tx, int slot, const Pack<T>& v) {
+    if (slot != cur) {
+      flush(cs, kp, tx);
+      cur = slot;
+#pragma unroll
+      for (int e = 0; e < N; ++e) acc[e] = T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < N; ++e) acc[e] += v.v[e];
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void slots_zero(const Geo& g, T* cs, int nsl, int kp) {
+  for (int i = g.tid; i < nsl * kp; i += g.nth) cs[i] = T(0);
+}
+template <typename T>
+__device__ __forceinline__ void slots_store(const Geo& g, const T* cs, int nsl, int kp,
+                                            T* dst) {
+  for (int i = g.tid; i < nsl * kp; i += g.nth) dst[i] = cs[i];
+}
+
+// x = 0, r = b, the fine r.z = b.D^{-1}b, ||b||^2 and the restriction of b; the coarse
+// kernel (INIT) then sets rz and the p update forms p = M^{-1} b
+template <typename T>
+__global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r,
+                          const T* __restrict__ dinv, int kp, int nc, int ncn, CgState s,
+                          Coarse<T> co) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
   int tile = blockIdx.x, sd = tl.sd[tile];
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  const bool coarse = co.aloc != nullptr;
+  T* cs = slot_smem<T>(g, kp);
+  int a0 = 0, nsl = 0;
+  if (coarse) {
+    a0 = co.aloc[r0];
+    nsl = co.aloc[r1 - 1] - a0 + 1;
+    slots_zero(g, cs, nsl, kp);
+    __syncthreads();
+  }
+  RestrictAcc<T> ra;
   T arz[N], arr[N];
 #pragma unroll
   for (int e = 0; e < N; ++e) arz[e] = arr[e] = T(0);
@@ -400,17 +461,21 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r, T* p,
   for (int e = 0; e < N; ++e) zero.v[e] = T(0);
   for (int64_t row = r0 + g.ty; row < r1; row += g.rb) {
     int64_t o = row * kp + g.tx * N;
-    Pack<T> bv = ld(b + o), pv;
+    Pack<T> bv = ld(b + o);
     T d = dinv[row];
 #pragma unroll
     for (int e = 0; e < N; ++e) {
-      pv.v[e] = d * bv.v[e];
-      arz[e] += bv.v[e] * pv.v[e];
+      arz[e] += bv.v[e] * (d * bv.v[e]);
       arr[e] += bv.v[e] * bv.v[e];
     }
+    if (coarse) ra.add(cs, kp, g.tx, co.aloc[row] - a0, bv);
     st(x + o, zero);
     st(r + o, bv);
-    st(p + o, pv);
+  }
+  if (coarse) {
+    ra.flush(cs, kp, g.tx);
+    __syncthreads();
+    slots_store(g, cs, nsl, kp, co.cpart + co.toff[tile] * kp);
   }
   block_colsum<T, N>(g, arz, sm.red, s.part1 + (int64_t)tile * kp);
   __syncthreads();
@@ -429,28 +494,40 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r, T* p,
   for (int c = g.tid; c < kp; c += g.nth) {
     int i = sd * kp + c;
     double bb = sm.sums[kp + c];
-    s.rz[i] = sm.sums[c];
+    s.rzf[i] = sm.sums[c];
     s.bb[i] = (c < ncn) ? bref : bb;
     s.rr[i] = bb;
     s.done[i] = (c >= nc || !(bb > 0.0)) ? 1 : 0;
     s.alpha[i] = 0.0;
     s.beta[i] = 0.0;
+    s.gam[i] = 1.0;
   }
   if (g.tid == 0) s.iters[sd] = 0;
   __syncthreads();
   count_active(g, s.done, sd, kp, s.active);
 }
 
-
+// x += alpha p, r -= alpha q; ||r||^2, the fine r.z = r.D^{-1}r and the restriction of
+// the new r; the coarse kernel (STEP) completes r.M^{-1}r, beta and the done flags
 template <typename T>
 __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
                                const T* __restrict__ q, const T* __restrict__ dinv, int kp,
-                               double tol2, CgState s) {
+                               CgState s, Coarse<T> co) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
   int tile = blockIdx.x, sd = tl.sd[tile];
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  const bool coarse = co.aloc != nullptr;
+  T* cs = slot_smem<T>(g, kp);
+  int a0 = 0, nsl = 0;
+  if (coarse) {
+    a0 = co.aloc[r0];
+    nsl = co.aloc[r1 - 1] - a0 + 1;
+    slots_zero(g, cs, nsl, kp);
+    __syncthreads();
+  }
+  RestrictAcc<T> ra;
   T al[N];
 #pragma unroll
   for (int e = 0; e < N; ++e) al[e] = (T)s.alpha[sd * kp + g.tx * N + e];
@@ -468,8 +545,14 @@ __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
       arr[e] += rv.v[e] * rv.v[e];
       arz[e] += rv.v[e] * (d * rv.v[e]);
     }
+    if (coarse) ra.add(cs, kp, g.tx, co.aloc[row] - a0, rv);
     st(x + o, xv);
     st(r + o, rv);
+  }
+  if (coarse) {
+    ra.flush(cs, kp, g.tx);
+    __syncthreads();
+    slots_store(g, cs, nsl, kp, co.cpart + co.toff[tile] * kp);
   }
   block_colsum<T, N>(g, arr, sm.red, s.part1 + (int64_t)tile * kp);
   __syncthreads();
@@ -480,42 +563,147 @@ __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
   sd_colsums(g, s.part2, kp, lo, hi, sm.scratch, sm.sums + kp);
   for (int c = g.tid; c < kp; c += g.nth) {
     int i = sd * kp + c;
-    double be = 0.0;
     s.rr[i] = sm.sums[c];
-    if (!s.done[i]) {
-      double rr = sm.sums[c], rzn = sm.sums[kp + c];
-      if (rr <= tol2 * s.bb[i] || !(s.rz[i] > 0.0)) {
-        s.done[i] = 1;
-      } else {
-        be = rzn / s.rz[i];
-        s.rz[i] = rzn;
+    s.rzf[i] = sm.sums[kp + c];
+  }
+}
+
+// Coarse level of one subdomain and a chunk of kCoarseCols columns (grid n_sd x chunks):
+// r_c = Z^T r from the tile partials, y_c = E^{-1} r_c (stored for the p update), and
+// r.M^{-1}r = fine part + r_c.y_c.  mode STEP: the convergence test on the recursive
+// residual and beta = (r.z)_new / (r.z)_old; INIT / REPLACE: rz only (beta and gam come
+// from the init / replacement kernel).  Without a coarse level y_c = 0.
+constexpr int kCoarseCols = 16;
+enum { kCoarseInit = 0, kCoarseStep = 1, kCoarseReplace = 2 };
+template <typename T>
+__global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s, Coarse<T> co) {
+  constexpr int CW = kCoarseCols;
+  Geo g = geo();
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* rc = reinterpret_cast<T*>(raw);  // n x CW
+  double* red = reinterpret_cast<double*>(raw + align16(sizeof(T) * kMaxAgg * CW));
+  __shared__ double cd[CW];
+  const int sd = blockIdx.x, c0 = blockIdx.y * CW;
+  const int n = co.aloc ? co.nca[sd] : 0;
+  const int a0 = n ? co.aoff[sd] : 0;
+  for (int idx = g.tid; idx < n * CW; idx += g.nth) {
+    int a = idx / CW, j = idx - a * CW, c = c0 + j;
+    T v = T(0);
+    if (c < kp) {
+      int ga = a0 + a;
+      int t0 = co.tfirst[ga], tn = co.tcount[ga];
+      for (int t = t0; t < t0 + tn; ++t) {
+        int slot = a - co.aloc[tl.r0[t]];
+        v += co.cpart[(co.toff[t] + slot) * kp + c];
       }
     }
-    s.beta[i] = be;
+    rc[idx] = v;
   }
   __syncthreads();
+  double dl[CW];
+#pragma unroll
+  for (int j = 0; j < CW; ++j) dl[j] = 0.0;
+  if (n > 0) {
+    const T* Eb = co.einv + co.eoff[sd];
+    for (int a = g.tid; a < n; a += g.nth) {
+      T acc[CW];
+#pragma unroll
+      for (int j = 0; j < CW; ++j) acc[j] = T(0);
+      for (int bidx = 0; bidx < n; ++bidx) {
+        T e = Eb[(int64_t)bidx * n + a];  // E^{-1} is symmetric: column a, coalesced
+        const T* rb = rc + bidx * CW;
+#pragma unroll
+        for (int j = 0; j < CW; ++j) acc[j] += e * rb[j];
+      }
+      T* yo = co.yc + (int64_t)(a0 + a) * kp + c0;
+#pragma unroll
+      for (int j = 0; j < CW; ++j) {
+        if (c0 + j < kp) yo[j] = acc[j];
+        dl[j] += (double)acc[j] * (double)rc[a * CW + j];
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CW; ++j) red[g.tid * CW + j] = dl[j];
+  __syncthreads();
+  if (g.tid < CW) {
+    double t = 0.0;
+    for (int q = 0; q < g.nth; ++q) t += red[q * CW + g.tid];  // fixed order
+    cd[g.tid] = t;
+  }
+  __syncthreads();
+  for (int j = g.tid; j < CW; j += g.nth) {
+    int c = c0 + j;
+    if (c >= kp) continue;
+    int i = sd * kp + c;
+    double rzn = s.rzf[i] + cd[j];
+    if (mode == kCoarseStep) {
+      double be = 0.0;
+      if (!s.done[i]) {
+        if (s.rr[i] <= tol2 * s.bb[i] || !(s.rz[i] > 0.0)) {
+          s.done[i] = 1;
+        } else {
+          be = rzn / s.rz[i];
+          s.rz[i] = rzn;
+        }
+      }
+      s.beta[i] = be;
+      s.gam[i] = 1.0;
+    } else {
+      s.rz[i] = rzn;
+    }
+  }
+  if (mode != kCoarseStep) return;
+  if (!last_block(g, s.counter, sd, gridDim.y)) return;
   count_active(g, s.done, sd, kp, s.active);
   if (g.tid == 0 && s.active[sd] > 0) s.iters[sd] += 1;
 }
 
+// p = gam (D^{-1} r + Z y_c) + beta p (p is not read where beta = 0), and p.r of the
+// new direction for the next step length
 template <typename T>
 __global__ void k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p,
-                              const T* __restrict__ dinv, int kp, CgState s) {
+                              const T* __restrict__ dinv, int kp, CgState s, Coarse<T> co) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
+  Smem<T> sm = smem_layout<T>(g, kp, 0);
   int tile = blockIdx.x, sd = tl.sd[tile];
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  T be[N];
+  const bool coarse = co.aloc != nullptr;
+  const int64_t a0 = coarse ? co.aoff[sd] : 0;
+  T be[N], ga[N];
+  bool needp = false;
 #pragma unroll
-  for (int e = 0; e < N; ++e) be[e] = (T)s.beta[sd * kp + g.tx * N + e];
+  for (int e = 0; e < N; ++e) {
+    be[e] = (T)s.beta[sd * kp + g.tx * N + e];
+    ga[e] = (T)s.gam[sd * kp + g.tx * N + e];
+    needp = needp || be[e] != T(0);
+  }
+  T apr[N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) apr[e] = T(0);
   for (int64_t row = r0 + g.ty; row < r1; row += g.rb) {
     int64_t o = row * kp + g.tx * N;
-    Pack<T> rv = ld(r + o), pv = ld(p + o);
+    Pack<T> rv = ld(r + o), pv, yv;
+    if (needp) pv = ld(p + o);
+    if (coarse) yv = ld(co.yc + (a0 + co.aloc[row]) * kp + g.tx * N);
     T d = dinv[row];
 #pragma unroll
-    for (int e = 0; e < N; ++e) pv.v[e] = d * rv.v[e] + be[e] * pv.v[e];
+    for (int e = 0; e < N; ++e) {
+      T z = d * rv.v[e];
+      if (coarse) z += yv.v[e];
+      T v = ga[e] * z;
+      if (be[e] != T(0)) v += be[e] * pv.v[e];
+      pv.v[e] = v;
+      apr[e] += v * rv.v[e];
+    }
     st(p + o, pv);
   }
+  block_colsum<T, N>(g, apr, sm.red, s.part1 + (int64_t)tile * kp);
+  int lo = tl.lo[sd], hi = tl.hi[sd];
+  if (!last_block(g, s.counter, sd, hi - lo)) return;
+  sd_colsums(g, s.part1, kp, lo, hi, sm.scratch, sm.sums);
+  for (int c = g.tid; c < kp; c += g.nth) s.pr[sd * kp + c] = sm.sums[c];
 }
 
 __global__ void k_count_active(int n_sd, const int* active, int* out) {
@@ -538,43 +726,51 @@ __global__ void k_zero_rows(DTiles tl, double* x, int kp) {
     for (int c = g.tx; c < kp; c += g.nch) x[row * kp + c] = 0.0;
 }
 
-// residual replacement: rT = (T) r64 (the true residual), rz recomputed from it, and
-// each column's done flag taken from the binary64 convergence test (scale == 0)
-// Columns the recursion had declared converged but the binary64 test reopens, and
-// columns whose true residual norm exceeds drift x the recursive one, restart from
-// p = D^{-1} r: their stored direction belongs to a much smaller residual.
+// residual replacement: rT = (T) r64 (the true residual), the fine r.z and the
+// restriction of it, each column's done flag from the binary64 convergence test
+// (scale == 0).  Columns the recursion had declared converged but the binary64 test
+// reopens, and columns whose true residual norm exceeds drift x the recursive one,
+// restart from p = M^{-1} r (their stored direction belongs to a much smaller
+// residual: gam = 1, beta = 0); the others keep p (gam = 0, beta = 1).  The coarse
+// kernel (REPLACE) then sets rz and the p update applies gam and beta.
 template <typename T>
 __global__ void k_cg_replace(DTiles tl, const double* __restrict__ r64, T* __restrict__ rT,
-                             T* __restrict__ pT, const T* __restrict__ dinv, int kp,
-                             double drift2, CgState s, RefineState rs) {
+                             const T* __restrict__ dinv, int kp, double drift2, CgState s,
+                             RefineState rs, Coarse<T> co) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
   int tile = blockIdx.x, sd = tl.sd[tile];
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  bool restart[N];
-#pragma unroll
-  for (int e = 0; e < N; ++e) {
-    int i = sd * kp + g.tx * N + e;
-    // reopened, or the recursion drifted from the true residual (a stale direction
-    // would make the next step length meaningless)
-    restart[e] = rs.scale[i] != 0.0 && (s.done[i] || rs.orr[i] > drift2 * s.rr[i]);
+  const bool coarse = co.aloc != nullptr;
+  T* cs = slot_smem<T>(g, kp);
+  int a0 = 0, nsl = 0;
+  if (coarse) {
+    a0 = co.aloc[r0];
+    nsl = co.aloc[r1 - 1] - a0 + 1;
+    slots_zero(g, cs, nsl, kp);
+    __syncthreads();
   }
+  RestrictAcc<T> ra;
   T arz[N];
 #pragma unroll
   for (int e = 0; e < N; ++e) arz[e] = T(0);
   for (int64_t row = r0 + g.ty; row < r1; row += g.rb) {
     int64_t o = row * kp + g.tx * N;
-    Pack<T> rv, pv = ld(pT + o);
+    Pack<T> rv;
     T d = dinv[row];
 #pragma unroll
     for (int e = 0; e < N; ++e) {
       rv.v[e] = (T)r64[o + e];
       arz[e] += rv.v[e] * (d * rv.v[e]);
-      if (restart[e]) pv.v[e] = d * rv.v[e];
     }
+    if (coarse) ra.add(cs, kp, g.tx, co.aloc[row] - a0, rv);
     st(rT + o, rv);
-    st(pT + o, pv);
+  }
+  if (coarse) {
+    ra.flush(cs, kp, g.tx);
+    __syncthreads();
+    slots_store(g, cs, nsl, kp, co.cpart + co.toff[tile] * kp);
   }
   block_colsum<T, N>(g, arz, sm.red, s.part1 + (int64_t)tile * kp);
   int lo = tl.lo[sd], hi = tl.hi[sd];
@@ -582,11 +778,16 @@ __global__ void k_cg_replace(DTiles tl, const double* __restrict__ r64, T* __res
   sd_colsums(g, s.part1, kp, lo, hi, sm.scratch, sm.sums);
   for (int c = g.tid; c < kp; c += g.nth) {
     int i = sd * kp + c;
-    s.rz[i] = sm.sums[c];
+    // reopened, or the recursion drifted from the true residual (a stale direction
+    // would make the next step length meaningless)
+    bool restart = rs.scale[i] != 0.0 && (s.done[i] || rs.orr[i] > drift2 * s.rr[i]);
+    bool done = rs.scale[i] == 0.0;
+    s.rzf[i] = sm.sums[c];
     s.bb[i] = rs.obb[i];
-    s.done[i] = (rs.scale[i] == 0.0) ? 1 : 0;
+    s.done[i] = done ? 1 : 0;
     s.alpha[i] = 0.0;
-    s.beta[i] = 0.0;
+    s.beta[i] = (done || restart) ? 0.0 : 1.0;
+    s.gam[i] = (done || restart) ? 1.0 : 0.0;
   }
   __syncthreads();
   count_active(g, s.done, sd, kp, s.active);
@@ -646,36 +847,72 @@ void launch_spmm(const DTiles& tiles, const EllView<T>& A, const T* X, T* Y, int
 }
 
 template <typename T>
+size_t slot_kernel_smem(dim3 bl, int kp) {
+  return slot_smem_bytes(smem_bytes<T>(bl.x, bl.y, kp, 0), kp, sizeof(T));
+}
+
+template <typename T>
+void launch_coarse_then_p(const DTiles& tiles, int n_sd, const T* r, T* p, const T* dinv,
+                          int kp, double tol2, int mode, const CgState& s, const Coarse<T>& co,
+                          cudaStream_t st, const cudaEvent_t* ev_mid) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute((const void*)k_cg_coarse<T>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  const int nthr = 256;
+  size_t sm = align16(sizeof(T) * kMaxAgg * kCoarseCols) + sizeof(double) * nthr * kCoarseCols;
+  dim3 grid(n_sd, (kp + kCoarseCols - 1) / kCoarseCols);
+  dim3 bl = block_of<T>(kp);
+  count_launch(2);
+  k_cg_coarse<T><<<grid, nthr, sm, st>>>(tiles, kp, tol2, mode, s, co);
+  if (ev_mid) cudaEventRecord(*ev_mid, st);
+  k_cg_update_p<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, r, p, dinv,
+                                                                         kp, s, co);
+}
+
+template <typename T>
 void launch_cg_init(const DTiles& tiles, const T* b, T* x, T* r, T* p, const T* dinv,
-                    int kp, int nc, int ncn, const CgState& s, cudaStream_t st) {
+                    int kp, int nc, int ncn, const CgState& s, const Coarse<T>& co,
+                    cudaStream_t st) {
   if (tiles.n <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    set_smem_attr<T>((const void*)k_cg_init<T>);
+    attr = true;
+  }
   dim3 bl = block_of<T>(kp);
   count_launch();
-  k_cg_init<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, b, x, r, p, dinv,
-                                                                      kp, nc, ncn, s);
+  k_cg_init<T><<<tiles.n, bl, slot_kernel_smem<T>(bl, kp), st>>>(tiles, b, x, r, dinv, kp, nc,
+                                                                  ncn, s, co);
+  launch_coarse_then_p<T>(tiles, tiles.n_sd, r, p, dinv, kp, 0.0, kCoarseInit, s, co, st,
+                          nullptr);
 }
 
 template <typename T>
 void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, T* q,
-                    const T* dinv, int kp, double tol2, const CgState& s, cudaStream_t st,
-                    const cudaEvent_t* ev) {
+                    const T* dinv, int kp, double tol2, const CgState& s, const Coarse<T>& co,
+                    cudaStream_t st, const cudaEvent_t* ev) {
   if (tiles.n <= 0) return;
   static bool attr = false;
   if (!attr) {
     set_smem_attr<T>((const void*)k_cg_spmm_pq<T>);
+    set_smem_attr<T>((const void*)k_cg_update_xr<T>);
     attr = true;
   }
   dim3 bl = block_of<T>(kp);
-  count_launch(3);
+  count_launch(2);
   if (ev) cudaEventRecord(ev[0], st);
   k_cg_spmm_pq<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, A.W), st>>>(tiles, A, p, q, kp,
                                                                            s);
   if (ev) cudaEventRecord(ev[1], st);
-  k_cg_update_xr<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, x, r, p, q,
-                                                                           dinv, kp, tol2, s);
+  k_cg_update_xr<T><<<tiles.n, bl, slot_kernel_smem<T>(bl, kp), st>>>(tiles, x, r, p, q, dinv,
+                                                                       kp, s, co);
   if (ev) cudaEventRecord(ev[2], st);
-  k_cg_update_p<T><<<tiles.n, bl, 0, st>>>(tiles, r, p, dinv, kp, s);
-  if (ev) cudaEventRecord(ev[3], st);
+  launch_coarse_then_p<T>(tiles, tiles.n_sd, r, p, dinv, kp, tol2, kCoarseStep, s, co, st,
+                          ev ? &ev[3] : nullptr);
+  if (ev) cudaEventRecord(ev[4], st);
 }
 
 void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st) {
@@ -707,12 +944,19 @@ void launch_residual64(const DTiles& tiles, const EllView<double>& A, const doub
 template <typename T>
 void launch_cg_replace(const DTiles& tiles, const double* r64, T* rT, T* pT, const T* dinv,
                        int kp, double drift, const CgState& s, const RefineState& rs,
-                       cudaStream_t st) {
+                       const Coarse<T>& co, cudaStream_t st) {
   if (tiles.n <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    set_smem_attr<T>((const void*)k_cg_replace<T>);
+    attr = true;
+  }
   dim3 bl = block_of<T>(kp);
   count_launch();
-  k_cg_replace<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(
-      tiles, r64, rT, pT, dinv, kp, drift * drift, s, rs);
+  k_cg_replace<T><<<tiles.n, bl, slot_kernel_smem<T>(bl, kp), st>>>(
+      tiles, r64, rT, dinv, kp, drift * drift, s, rs, co);
+  launch_coarse_then_p<T>(tiles, tiles.n_sd, rT, pT, dinv, kp, 0.0, kCoarseReplace, s, co, st,
+                          nullptr);
 }
 
 template <typename T>
@@ -731,10 +975,11 @@ void launch_cast(const DTiles& tiles, const double* src, T* dst, int kp, cudaStr
 
 template void launch_cg_replace<float>(const DTiles&, const double*, float*, float*,
                                        const float*, int, double, const CgState&,
-                                       const RefineState&, cudaStream_t);
+                                       const RefineState&, const Coarse<float>&, cudaStream_t);
 template void launch_cg_replace<double>(const DTiles&, const double*, double*, double*,
                                         const double*, int, double, const CgState&,
-                                        const RefineState&, cudaStream_t);
+                                        const RefineState&, const Coarse<double>&,
+                                        cudaStream_t);
 template void launch_accum_reset<float>(const DTiles&, float*, double*, int, cudaStream_t);
 template void launch_accum_reset<double>(const DTiles&, double*, double*, int, cudaStream_t);
 template void launch_cast<float>(const DTiles&, const double*, float*, int, cudaStream_t);
@@ -751,14 +996,16 @@ template void launch_spmm<float>(const DTiles&, const EllView<float>&, const flo
 template void launch_spmm<double>(const DTiles&, const EllView<double>&, const double*,
                                   double*, int, cudaStream_t);
 template void launch_cg_init<float>(const DTiles&, const float*, float*, float*, float*,
-                                    const float*, int, int, int, const CgState&, cudaStream_t);
+                                    const float*, int, int, int, const CgState&,
+                                    const Coarse<float>&, cudaStream_t);
 template void launch_cg_init<double>(const DTiles&, const double*, double*, double*, double*,
                                      const double*, int, int, int, const CgState&,
-                                     cudaStream_t);
+                                     const Coarse<double>&, cudaStream_t);
 template void launch_cg_step<float>(const DTiles&, const EllView<float>&, float*, float*,
                                     float*, float*, const float*, int, double, const CgState&,
-                                    cudaStream_t, const cudaEvent_t*);
+                                    const Coarse<float>&, cudaStream_t, const cudaEvent_t*);
 template void launch_cg_step<double>(const DTiles&, const EllView<double>&, double*, double*,
                                      double*, double*, const double*, int, double,
-                                     const CgState&, cudaStream_t, const cudaEvent_t*);
+                                     const CgState&, const Coarse<double>&, cudaStream_t,
+                                     const cudaEvent_t*);
 }  // namespace mor

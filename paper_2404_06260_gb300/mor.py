@@ -39,7 +39,8 @@ class BasisOpts(ctypes.Structure):
                 ("precision", _i32), ("sketch", _i32), ("cg_rtol", _dbl),
                 ("max_iter", _i32), ("replace_every", _i32), ("normwise", _i32),
                 ("drift_restart", _dbl),
-                ("sketch_rtol", _dbl), ("tau", _dbl), ("orth_tol", _dbl)]
+                ("sketch_rtol", _dbl), ("tau", _dbl), ("orth_tol", _dbl),
+                ("coarse_rows", _i32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -298,7 +299,8 @@ def profile_query(family: int):
 
 
 KERNEL_FAMILIES = {0: "cg_spmm_pq<f32>", 1: "cg_spmm_pq<f64>", 2: "cg_update_xr<f32>",
-                   3: "cg_update_xr<f64>", 4: "cg_update_p<f32>", 5: "cg_update_p<f64>"}
+                   3: "cg_update_xr<f64>", 4: "cg_update_p<f32>", 5: "cg_update_p<f64>",
+                   6: "cg_coarse<f32>", 7: "cg_coarse<f64>"}
 
 
 def kernel_launches() -> int:
