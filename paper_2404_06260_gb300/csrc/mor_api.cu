@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <array>
 #include <atomic>
 #include <cmath>
@@ -45,18 +46,50 @@ int fail(int code, const std::string& msg) {
     if (rc_ != MOR_OK) return rc_; \
   } while (0)
 
+// Device allocations owned by one object.  Handle memory uses cudaMalloc.  A call's
+// workspace is "pooled": stream-ordered allocations from the device's default memory
+// pool on the call's stream, freed on that stream when the workspace goes out of
+// scope, so repeated calls reuse memory without cudaMalloc/cudaFree synchronisation.
+void keep_default_pool_warm() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool (this process only)
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done.push_back(dev);
+}
+
 struct Allocs {
   std::vector<void*> ptrs;
+  bool pooled = false;
+  cudaStream_t pool_st = nullptr;
   Allocs() = default;
   Allocs(const Allocs&) = delete;
   Allocs& operator=(const Allocs&) = delete;
+  void use_pool(cudaStream_t st) {
+    keep_default_pool_warm();
+    pooled = true;
+    pool_st = st;
+  }
   ~Allocs() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) {
+      if (pooled)
+        cudaFreeAsync(p, pool_st);
+      else
+        cudaFree(p);
+    }
   }
   template <class T>
   int alloc(T** p, size_t n, bool zero = true, cudaStream_t st = nullptr) {
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    cudaError_t e = pooled ? cudaMallocAsync((void**)p, n * sizeof(T), pool_st)
+                           : cudaMalloc((void**)p, n * sizeof(T));
     if (e != cudaSuccess) {
       *p = nullptr;
       return fail(e == cudaErrorMemoryAllocation ? MOR_ERR_OOM : MOR_ERR_CUDA,
@@ -365,12 +398,15 @@ struct Build {
     if (h_poll) cudaFreeHost(h_poll);
   }
 
-  int poll(const int* active) {
-    launch_count_active(n_sd, active, d_poll, st);
-    CK(cudaMemcpyAsync(h_poll, d_poll, sizeof(int), cudaMemcpyDeviceToHost, st));
+  // sum of active[] over the subdomains (and of second[] into h_poll[1])
+  int poll(const int* active, const int* second = nullptr) {
+    launch_count_active(n_sd, active, d_poll, st, second);
+    CK(cudaMemcpyAsync(h_poll, d_poll, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    return *h_poll;
+    return h_poll[0];
   }
+  // per matrix set: max row sum of |A| per subdomain (rounding-level bound)
+  double* anorm[2] = {nullptr, nullptr};
 
   // coarse levels of the two-level preconditioner: [0] A_II (I tiles), [1] H^+ (all P
   // tiles); cbytes = algorithmic bytes of one coarse kernel launch per set
@@ -411,13 +447,14 @@ struct Build {
     // replace_every iterations and whenever the recursion reports convergence
     // (residual replacement keeps the search directions, so no Krylov restart)
     launch_zero_rows(tl, x64, kp, st);
-    launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 1, false, rs, st);
+    launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 1, false, anorm[set],
+                      rs, st);
     if (poll(rs.active) == 0) return MOR_OK;
     launch_cast<T>(tl, vR64, b, kp, st);
     launch_cg_init<T>(tl, b, x, r, p, dinvT, kp, nc, ncn, cs, co, st);
     const int check = 8;
     const int every = std::max(check, o->replace_every / check * check);
-    int it = 0, nsweep = 0;
+    int it = 0;
     while (true) {
       int chunk = std::min(check, o->max_iter - it);
       for (int c = 0; c < chunk; ++c) {
@@ -434,12 +471,18 @@ struct Build {
       int act = poll(cs.active);
       if (act == 0 || it % every == 0 || it >= o->max_iter) {
         launch_accum_reset<T>(tl, x, x64, kp, st);
-        // the rounding-level reference is refreshed on sweeps 1, 2, 4, 8, ...
-        ++nsweep;
-        const bool refresh = (nsweep & (nsweep - 1)) == 0;
-        launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 0, refresh, rs, st);
+        launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 0, false,
+                          anorm[set], rs, st);
         ++sweeps;
-        int ract = poll(rs.active);
+        int ract = poll(rs.active, rs.nnear);
+        if (ract > 0 && h_poll[1] > 0) {
+          // some open column is within reach of the rounding level: measure the exact
+          // reference || |A| |x| + |b| || and test again
+          launch_residual64(tl, A.e64(), b64, x64, vR64, kp, nc, ncn, rtol2, 0, true,
+                            anorm[set], rs, st);
+          ++sweeps;
+          ract = poll(rs.active);
+        }
         if (debug) {
           std::vector<double> orr((size_t)n_sd * kp), obb((size_t)n_sd * kp);
           cudaMemcpy(orr.data(), rs.orr, orr.size() * sizeof(double), cudaMemcpyDeviceToHost);
@@ -556,6 +599,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   B.m = mcols;
   B.mixed = o.precision == MOR_MIXED;
   Allocs& M = B.mem;
+  M.use_pool(st);
   const int n_sd = hp.n_sd;
   const int64_t nP = hp.nP, nW = hp.nW, nO = hp.nO;
   const int WP = hp.pat_P.W, WW = hp.pat_W.W;
@@ -564,8 +608,8 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   const int64_t nEllO = ceil_div(nO, 32) * 32 * WW;
   const int64_t nIncP = (int64_t)hp.incP_tet.size();
 
-  CK(cudaMallocHost((void**)&B.h_poll, sizeof(int)));
-  TRY(M.alloc(&B.d_poll, 1, true, st));
+  CK(cudaMallocHost((void**)&B.h_poll, 2 * sizeof(int)));
+  TRY(M.alloc(&B.d_poll, 2, true, st));
   int* d_err;
   TRY(M.alloc(&d_err, 1, true, st));
 
@@ -746,8 +790,16 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.alloc(&B.rs.scale, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.rs.part, (size_t)mt * kp, true, st));
   TRY(M.alloc(&B.rs.part2, (size_t)mt * kp, true, st));
+  TRY(M.alloc(&B.rs.part3, (size_t)mt * kp, true, st));
   TRY(M.alloc(&B.rs.oaa, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.rs.nfloor, n_sd, true, st));
+  TRY(M.alloc(&B.rs.nnear, n_sd, true, st));
+  TRY(M.alloc(&B.rs.xx, (size_t)n_sd * kp, true, st));
+  for (int set = 0; set < 2; ++set) {
+    TRY(M.alloc(&B.anorm[set], n_sd, true, st));
+    launch_row_abs_max(set == 0 ? S.tP_I : S.tP_all, set == 0 ? A_II.e64() : Hp.e64(),
+                       B.anorm[set], st);
+  }
   TRY(M.alloc(&B.rs.counter, n_sd, true, st));
   TRY(M.alloc(&B.rs.active, n_sd, true, st));
   double *Xw, *Yw, *Zw, *u0w, *V, *AV, *bP;
@@ -984,6 +1036,7 @@ int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void*
     return fail(MOR_ERR_ARG, "mor_solve_reduced: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
   Allocs A;
+  A.use_pool(st);
   RcgState s{};
   s.x = x_dev;
   TRY(A.alloc(&s.r, h->dim, false, st));

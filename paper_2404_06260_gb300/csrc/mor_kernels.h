@@ -130,17 +130,21 @@ template <typename T>
 void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, T* q,
                     const T* dinv, int kp, double tol2, const CgState& s,
                     const Coarse<T>& co, cudaStream_t st, const cudaEvent_t* ev = nullptr);
-void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st);
+// out[0] = sum of active[0..n_sd), out[1] = sum of second (0 if null); out has 2 ints
+void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st,
+                         const int* second = nullptr);
 
 // binary64 residual: r64 = b64 - A64 x64 with per-column norms; scale = 1/||r64|| for
 // columns with ||r64|| > rtol ||b64|| (0 = converged); first = 1 records ||b64||.
 struct RefineState {
   double *obb, *orr, *scale;  // n_sd x kp
   double* oaa;                // n_sd x kp: || |A| |x| + |b| ||^2 at the last refresh
-  double *part, *part2;       // n_tiles x kp
+  double *part, *part2, *part3;  // n_tiles x kp
   int* counter;               // n_sd
   int* active;                // n_sd
   int* nfloor;                // n_sd: columns stopped by the attainable-accuracy test
+  int* nnear;                 // n_sd: open columns within reach of that test
+  double* xx;                 // n_sd x kp: ||x64||^2 of the last residual sweep
 };
 // a binary64 residual below kResidualFloor * 2^-53 * || |A| |x| + |b| ||_2 is rounding
 // noise of its own evaluation; launch_residual64 stops such columns
@@ -148,10 +152,16 @@ constexpr double kResidualFloor = 4.0;
 // r64 = b - A x64 per column, the binary64 convergence test (rtol, or the rounding level
 // of the residual itself), done flags in s.scale; first = 1 also fixes the references
 // from b (x64 = 0).  floor_ref = true refreshes the rounding-level reference
-// || |A| |x| + |b| || (one extra binary64 add per product)
+// || |A| |x| + |b| || (one extra binary64 add per product).  s.nnear counts the open
+// columns whose residual is within the rounding level of the bound
+// anorm[sd] ||x|| + ||b|| (anorm = max row sum of |A|; ||x|| of this sweep).
 void launch_residual64(const DTiles& tiles, const EllView<double>& A, const double* b64,
                        const double* x64, double* r64, int kp, int nc, int ncn, double rtol2,
-                       int first, bool floor_ref, const RefineState& s, cudaStream_t st);
+                       int first, bool floor_ref, const double* anorm, const RefineState& s,
+                       cudaStream_t st);
+// anorm[sd] = max over the rows of tiles in sd of sum_j |a_ij| (anorm zeroed by caller)
+void launch_row_abs_max(const DTiles& tiles, const EllView<double>& A, double* anorm,
+                        cudaStream_t st);
 void launch_zero_rows(const DTiles& tiles, double* x, int kp, cudaStream_t st);
 // residual replacement of the CG recursion: rT = (T) r64, rz recomputed, done flags from
 // the binary64 convergence test of launch_residual64 (scale == 0 means converged);

@@ -306,7 +306,8 @@ __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
 template <bool kFloor>
 __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restrict__ b,
                              const double* __restrict__ x, double* __restrict__ r, int kp,
-                             int nc, int ncn, double rtol2, int first, RefineState s) {
+                             int nc, int ncn, double rtol2, int first, RefineState s,
+                             const double* __restrict__ anorm) {
   constexpr int N = 2;
   Geo g = geo();
   Smem<double> sm = smem_layout<double>(g, kp, A.W);
@@ -314,10 +315,15 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
   const int r0 = tl.r0[tile], r1 = tl.r1[tile];
   stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
   __syncthreads();
-  double acc[N] = {0.0, 0.0}, aca[N] = {0.0, 0.0};
+  double acc[N] = {0.0, 0.0}, aca[N] = {0.0, 0.0}, axx[N] = {0.0, 0.0};
   for (int rr = g.ty; rr < r1 - r0; rr += g.rb) {
     int64_t row = r0 + rr;
     Pack<double> ax, aabs;
+    {
+      Pack<double> xo = ld(x + row * kp + g.tx * N);
+#pragma unroll
+      for (int e = 0; e < N; ++e) axx[e] += xo.v[e] * xo.v[e];
+    }
     if constexpr (kFloor)
       spmm_row_res(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, x, kp, ax, aabs);
     else
@@ -336,6 +342,8 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
     st(r + o, rv);
   }
   block_colsum<double, N>(g, acc, sm.red, s.part + (int64_t)tile * kp);
+  __syncthreads();
+  block_colsum<double, N>(g, axx, sm.red, s.part3 + (int64_t)tile * kp);
   if constexpr (kFloor) {
     __syncthreads();
     block_colsum<double, N>(g, aca, sm.red, s.part2 + (int64_t)tile * kp);
@@ -346,12 +354,16 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
   if constexpr (kFloor) {
     sd_colsums(g, s.part2, kp, lo, hi, sm.scratch, sm.sums + kp);
     for (int c = g.tid; c < kp; c += g.nth) s.oaa[sd * kp + c] = sm.sums[kp + c];
+    __syncthreads();
   }
-  __shared__ int cnt, nfl;
+  sd_colsums(g, s.part3, kp, lo, hi, sm.scratch, sm.sums + kp);
+  for (int c = g.tid; c < kp; c += g.nth) s.xx[sd * kp + c] = sm.sums[kp + c];
+  __shared__ int cnt, nfl, nnear;
   __shared__ double bref;
   if (g.tid == 0) {
     cnt = 0;
     nfl = 0;
+    nnear = 0;
     double m = 0.0;
     if (first)
       for (int c = 0; c < ncn; ++c) m = fmax(m, sm.sums[c]);
@@ -378,11 +390,19 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
     s.scale[i] = done ? 0.0 : 1.0 / sqrt(rr);
     if (!done) atomicAdd(&cnt, 1);
     if (c < nc && s.obb[i] > 0.0 && !by_rtol && by_floor) atomicAdd(&nfl, 1);
+    // || |A| |x| + |b| || <= ||A||_inf ||x|| + ||b|| (A symmetric): a column above
+    // that bound's rounding level cannot stop on the floor test, so the reference
+    // needs refreshing only when some open column is below it
+    if (!done && !first) {
+      double bnd = anorm[sd] * sqrt(s.xx[i]) + sqrt(s.obb[i]);
+      if (rr <= fl2 * bnd * bnd) atomicAdd(&nnear, 1);
+    }
   }
   __syncthreads();
   if (g.tid == 0) {
     s.active[sd] = cnt;
     s.nfloor[sd] = nfl;
+    s.nnear[sd] = nnear;
   }
 }
 
@@ -586,18 +606,33 @@ __global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s,
   const int sd = blockIdx.x, c0 = blockIdx.y * CW;
   const int n = co.aloc ? co.nca[sd] : 0;
   const int a0 = n ? co.aoff[sd] : 0;
-  for (int idx = g.tid; idx < n * CW; idx += g.nth) {
-    int a = idx / CW, j = idx - a * CW, c = c0 + j;
-    T v = T(0);
-    if (c < kp) {
-      int ga = a0 + a;
-      int t0 = co.tfirst[ga], tn = co.tcount[ga];
+  // r_c = Z^T r: thread a sums the partial rows of aggregate a over the tiles holding
+  // it (contiguous 16-byte packs of this column chunk; kp and c0 are multiples of the
+  // pack width).  Rows n .. round_up(n, 8) are zero: the product below runs in steps
+  // of 8.
+  constexpr int PN = Pack<T>::N;
+  const int n8 = (n + 7) & ~7;
+  for (int a = g.tid; a < n8; a += g.nth) {
+    T v[CW];
+#pragma unroll
+    for (int j = 0; j < CW; ++j) v[j] = T(0);
+    if (a < n) {
+      const int ga = a0 + a;
+      const int t0 = co.tfirst[ga], tn = co.tcount[ga];
       for (int t = t0; t < t0 + tn; ++t) {
-        int slot = a - co.aloc[tl.r0[t]];
-        v += co.cpart[(co.toff[t] + slot) * kp + c];
+        const int slot = a - co.aloc[tl.r0[t]];
+        const T* src = co.cpart + (co.toff[t] + slot) * kp + c0;
+#pragma unroll
+        for (int j = 0; j < CW; j += PN)
+          if (c0 + j < kp) {
+            Pack<T> pv = ld(src + j);
+#pragma unroll
+            for (int e = 0; e < PN; ++e) v[j + e] += pv.v[e];
+          }
       }
     }
-    rc[idx] = v;
+#pragma unroll
+    for (int j = 0; j < CW; ++j) rc[a * CW + j] = v[j];
   }
   __syncthreads();
   double dl[CW];
@@ -609,11 +644,19 @@ __global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s,
       T acc[CW];
 #pragma unroll
       for (int j = 0; j < CW; ++j) acc[j] = T(0);
-      for (int bidx = 0; bidx < n; ++bidx) {
-        T e = Eb[(int64_t)bidx * n + a];  // E^{-1} is symmetric: column a, coalesced
-        const T* rb = rc + bidx * CW;
+      // E^{-1} is symmetric: thread a reads column a (coalesced across threads); eight
+      // loads are issued before their multiply-adds
+      for (int b0 = 0; b0 < n; b0 += 8) {
+        T e[8];
 #pragma unroll
-        for (int j = 0; j < CW; ++j) acc[j] += e * rb[j];
+        for (int u = 0; u < 8; ++u)
+          e[u] = (b0 + u < n) ? Eb[(int64_t)(b0 + u) * n + a] : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const T* rb = rc + (b0 + u) * CW;
+#pragma unroll
+          for (int j = 0; j < CW; ++j) acc[j] += e[u] * rb[j];
+        }
       }
       T* yo = co.yc + (int64_t)(a0 + a) * kp + c0;
 #pragma unroll
@@ -706,15 +749,23 @@ __global__ void k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p,
   for (int c = g.tid; c < kp; c += g.nth) s.pr[sd * kp + c] = sm.sums[c];
 }
 
-__global__ void k_count_active(int n_sd, const int* active, int* out) {
-  __shared__ int tot;
-  if (threadIdx.x == 0) tot = 0;
+// out[0] = sum of active, out[1] = sum of second (if not null)
+__global__ void k_count_active(int n_sd, const int* active, const int* second, int* out) {
+  __shared__ int tot, tot2;
+  if (threadIdx.x == 0) tot = tot2 = 0;
   __syncthreads();
-  int a = 0;
-  for (int i = threadIdx.x; i < n_sd; i += blockDim.x) a += active[i];
+  int a = 0, b = 0;
+  for (int i = threadIdx.x; i < n_sd; i += blockDim.x) {
+    a += active[i];
+    if (second) b += second[i];
+  }
   atomicAdd(&tot, a);
+  atomicAdd(&tot2, b);
   __syncthreads();
-  if (threadIdx.x == 0) *out = tot;
+  if (threadIdx.x == 0) {
+    out[0] = tot;
+    out[1] = tot2;
+  }
 }
 
 
@@ -805,6 +856,23 @@ __global__ void k_accum_reset(DTiles tl, T* __restrict__ xT, double* __restrict_
       x64[o] += (double)xT[o];
       xT[o] = T(0);
     }
+}
+
+// per subdomain: max over its rows of sum_j |a_ij| (nonnegative doubles order like
+// their bit patterns, so an integer atomicMax is exact); out zeroed by the caller
+__global__ void k_row_abs_max(DTiles tl, EllView<double> A, unsigned long long* out) {
+  const int tile = blockIdx.x, sd = tl.sd[tile];
+  const int64_t row = tl.r0[tile] + (int64_t)threadIdx.x;
+  double sum = 0.0;
+  if (row < tl.r1[tile]) {
+    const int w = A.width[row >> 5];
+    for (int j = 0; j < w; ++j) {
+      int64_t at = ell_at(row, j, A.W);
+      if (A.col[at] >= 0) sum += fabs(A.val[at]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sum = fmax(sum, __shfl_xor_sync(0xFFFFFFFFu, sum, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out + sd, (unsigned long long)__double_as_longlong(sum));
 }
 
 // rT = (T) src
@@ -915,14 +983,16 @@ void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, 
   if (ev) cudaEventRecord(ev[4], st);
 }
 
-void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st) {
+void launch_count_active(int n_sd, const int* active, int* out, cudaStream_t st,
+                         const int* second) {
   count_launch();
-  k_count_active<<<1, 256, 0, st>>>(n_sd, active, out);
+  k_count_active<<<1, 256, 0, st>>>(n_sd, active, second, out);
 }
 
 void launch_residual64(const DTiles& tiles, const EllView<double>& A, const double* b64,
                        const double* x64, double* r64, int kp, int nc, int ncn, double rtol2,
-                       int first, bool floor_ref, const RefineState& s, cudaStream_t st) {
+                       int first, bool floor_ref, const double* anorm, const RefineState& s,
+                       cudaStream_t st) {
   if (tiles.n <= 0) return;
   static bool attr = false;
   if (!attr) {
@@ -935,10 +1005,10 @@ void launch_residual64(const DTiles& tiles, const EllView<double>& A, const doub
   count_launch();
   if (floor_ref && !first)
     k_residual64<true><<<tiles.n, bl, sm, st>>>(tiles, A, b64, x64, r64, kp, nc, ncn, rtol2,
-                                                first, s);
+                                                first, s, anorm);
   else
     k_residual64<false><<<tiles.n, bl, sm, st>>>(tiles, A, b64, x64, r64, kp, nc, ncn, rtol2,
-                                                 first, s);
+                                                 first, s, anorm);
 }
 
 template <typename T>
@@ -964,6 +1034,13 @@ void launch_accum_reset(const DTiles& tiles, T* xT, double* x64, int kp, cudaStr
   if (tiles.n <= 0) return;
   count_launch();
   k_accum_reset<T><<<tiles.n, dim3(32, 8), 0, st>>>(tiles, xT, x64, kp);
+}
+
+void launch_row_abs_max(const DTiles& tiles, const EllView<double>& A, double* out,
+                        cudaStream_t st) {
+  if (tiles.n <= 0) return;
+  count_launch();
+  k_row_abs_max<<<tiles.n, kTileRows, 0, st>>>(tiles, A, (unsigned long long*)out);
 }
 
 template <typename T>
