@@ -255,10 +255,13 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts,
  * kind 0 = sparse product q = A p with the p.q column sums, 1 = x/r update with the
  * r.r and fine r.z sums and the restriction Z^T r, 2 = p update with the
  * prolongation and the p.r sums, 3 = coarse solve E^{-1} Z^T r; wide 0 = binary32,
- * 1 = binary64 (families 0..7).  Algorithmic bytes count every stored nonzero (value
- * + column index) and every vector block element the kernel must read or write once
- * (the coarse kernel: its E^{-1} blocks once per 16-column chunk).  Process-wide
- * state, not thread-safe. */
+ * 1 = binary64 (families 0..7).  Algorithmic bytes count the work actually done
+ * (subdomains and 16-byte column packs whose columns have all converged are skipped):
+ * every stored nonzero (value + column index) of an active subdomain's sparse
+ * product, and every element of an open pack the kernel must read or write once (the
+ * coarse kernel: its E^{-1} blocks once per open 16-column chunk); diagonal,
+ * aggregate-index and coarse-correction reads are not counted.  Process-wide state,
+ * not thread-safe. */
 int mor_profile_enable(int32_t on);
 int mor_profile_reset(void);
 int mor_profile_query(int32_t family, double* out);

@@ -407,12 +407,14 @@ struct Build {
   }
   // per matrix set: max row sum of |A| per subdomain (rounding-level bound)
   double* anorm[2] = {nullptr, nullptr};
+  // per matrix set (profiling only): rows and stored entries of each subdomain
+  int32_t* sd_rows[2] = {nullptr, nullptr};
+  int64_t* sd_nnz[2] = {nullptr, nullptr};
 
   // coarse levels of the two-level preconditioner: [0] A_II (I tiles), [1] H^+ (all P
-  // tiles); cbytes = algorithmic bytes of one coarse kernel launch per set
+  // tiles)
   Coarse<float> co32[2];
   Coarse<double> co64[2];
-  double cbytes[2] = {0, 0};
   template <typename T>
   const Coarse<T>& coarse_of(int set) const {
     if constexpr (sizeof(T) == 4)
@@ -425,6 +427,8 @@ struct Build {
   int solve(const DTiles& tl, const Mat& A, const T* dinvT, const double* b64, double* x64,
             int nc, int which, double rtol, int set) {
     const Coarse<T>& co = coarse_of<T>(set);
+    cs.sd_rows = sd_rows[set];
+    cs.sd_nnz = sd_nnz[set];
     // columns [0, ncn) share the block-normwise reference; the load column (forward
     // solve, column k) keeps its own
     const int ncn = o->normwise ? std::min(nc, k) : 0;
@@ -440,8 +444,8 @@ struct Build {
     T* b = (T*)bT;
     double rtol2 = rtol * rtol;
     double pb[4] = {0, 0, 0, 0};
-    if (g_prof.on) prof_bytes(tl, A, sizeof(T), pb);
-    pb[3] = cbytes[set] * (double)sizeof(T);
+    // bytes come from the device work counters (cs.work), attributed when the build
+    // finishes; the events time every launch
     // one CG per (subdomain, column) in precision T on the full system, with the
     // recursively updated residual replaced by the binary64 residual b - A x64 every
     // replace_every iterations and whenever the recursion reports convergence
@@ -497,6 +501,16 @@ struct Build {
           fprintf(stderr, "[mor] solve %d it %d active %d recursive-active %d worst %.3e (sd %d col %d)\n",
                   which, it, ract, act, std::sqrt(worst), wi / kp, wi % kp);
         }
+        if (debug && (ract == 0 || it >= o->max_iter)) {
+          std::vector<int> its(n_sd);
+          cudaMemcpy(its.data(), cs.iters, n_sd * sizeof(int), cudaMemcpyDeviceToHost);
+          std::sort(its.begin(), its.end());
+          long tot = 0;
+          for (int v : its) tot += v;
+          fprintf(stderr, "[mor] solve %d recursion iterations per subdomain: min %d median %d max %d "
+                  "(busy fraction %.2f)\n", which, its.front(), its[n_sd / 2], its.back(),
+                  (double)tot / ((double)n_sd * std::max(1, it)));
+        }
         if (ract == 0 || it >= o->max_iter) {
           // columns that ended on the attainable-accuracy test instead of rtol
           std::vector<int> nfl(n_sd);
@@ -515,44 +529,7 @@ struct Build {
     return MOR_OK;
   }
 
-  // algorithmic bytes of the kernels of one CG step on the rows of tl:
-  // sparse product = every stored nonzero (value + column index) once + read p and
-  // write q once; x/r update = read x, r, p, q and write x, r (+ the diagonal);
-  // p update = read r, p and write p (+ the diagonal); coarse kernel = its E^{-1}
-  // blocks once per column chunk (set in cbytes)
-  std::vector<double> nnz_by_mat;
-  const Mat* mats[8] = {};
-  double rows_of(const DTiles& tl) const;
-  void prof_bytes(const DTiles& tl, const Mat& A, size_t tsz, double out[4]) {
-    double nnz = 0;
-    for (int i = 0; i < 8; ++i)
-      if (mats[i] == &A) nnz = nnz_by_mat[i];
-    double rows = rows_of(tl);
-    out[0] = nnz * (tsz + 4.0) + rows * kp * tsz * 2.0;
-    out[1] = rows * kp * tsz * 6.0 + rows * tsz;
-    out[2] = rows * kp * tsz * 3.0 + rows * tsz;
-  }
 };
-
-double Build::rows_of(const DTiles& tl) const {
-  const HostPlan& hp = S->hp;
-  const HostTiles* ht = nullptr;
-  if (tl.sd == S->tP_I.sd) ht = &hp.tP_I;
-  else if (tl.sd == S->tP_all.sd) ht = &hp.tP_all;
-  else if (tl.sd == S->tP_B.sd) ht = &hp.tP_B;
-  else if (tl.sd == S->tW.sd) ht = &hp.tW;
-  else ht = &hp.tO;
-  double n = 0;
-  for (size_t t = 0; t < ht->r0.size(); ++t) n += ht->r1[t] - ht->r0[t];
-  return n;
-}
-
-__global__ void k_count_nnz(int64_t n, const int32_t* col, unsigned long long* out) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  unsigned long long c = (i < n && col[i] >= 0) ? 1ull : 0ull;
-  unsigned m = __ballot_sync(0xFFFFFFFFu, c != 0);
-  if ((threadIdx.x & 31) == 0 && m) atomicAdd(out, (unsigned long long)__popc(m));
-}
 
 }  // namespace
 
@@ -663,20 +640,6 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
                  -1.0, WW, Hi.width, Hi.col, Hi.v64, nullptr, nullptr, nullptr, st);
   launch_extract(nO, S.o2w, nullptr, 0, S.patW_col, S.patW_w, WW, valA_W, S.w2o, nullptr, 0,
                  drop, WW, App.width, App.col, App.v64, nullptr, nullptr, nullptr, st);
-  {
-    // nonzero counts for the algorithmic-bytes model of the timed kernels
-    unsigned long long* d_cnt;
-    TRY(M.alloc(&d_cnt, 2, true, st));
-    count_launch(2);
-    k_count_nnz<<<(unsigned)ceil_div(nEllP, 256), 256, 0, st>>>(nEllP, A_II.col, d_cnt);
-    k_count_nnz<<<(unsigned)ceil_div(nEllP, 256), 256, 0, st>>>(nEllP, Hp.col, d_cnt + 1);
-    unsigned long long hc[2];
-    CK(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    B.nnz_by_mat = {(double)hc[0], (double)hc[1]};
-    B.mats[0] = &A_II;
-    B.mats[1] = &Hp;
-  }
   int h_err = 0;
   CK(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -697,7 +660,6 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
     TRY(M.alloc((unsigned char**)&yc, (size_t)n_agg * kp * tsz_c, true, st));
     int* d_bad;
     TRY(M.alloc(&d_bad, 1, true, st));
-    const int nchunk = (kp + 15) / 16;
     for (int set = 0; set < 2; ++set) {
       const DTiles& tl = set == 0 ? S.tP_I : S.tP_all;
       const Mat& Am = set == 0 ? A_II : Hp;
@@ -720,7 +682,6 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
         launch_coarse_invert<float>(n_sd, nca, eoff, E, (float*)einv, d_bad, st);
       else
         launch_coarse_invert<double>(n_sd, nca, eoff, E, (double*)einv, d_bad, st);
-      B.cbytes[set] = (double)ne * nchunk;
       auto fill = [&](auto& c, auto* ei, auto* cp, auto* y) {
         c.aloc = aloc;
         c.aoff = aoff;
@@ -745,7 +706,6 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
       for (int set = 0; set < 2; ++set) {
         B.co32[set] = Coarse<float>();
         B.co64[set] = Coarse<double>();
-        B.cbytes[set] = 0;
       }
   }
 
@@ -779,6 +739,19 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.alloc(&B.cs.rzf, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.gam, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.pr, (size_t)n_sd * kp, true, st));
+  if (g_prof.on) {
+    // work counters and, per matrix set, rows and stored entries of every subdomain
+    TRY(M.alloc(&B.cs.work, (size_t)4 * n_sd, true, st));
+    for (int set = 0; set < 2; ++set) {
+      const HostTiles& ht = set == 0 ? hp.tP_I : hp.tP_all;
+      std::vector<int32_t> rows(n_sd, 0);
+      for (size_t t = 0; t < ht.sd.size(); ++t) rows[ht.sd[t]] += ht.r1[t] - ht.r0[t];
+      TRY(M.upload(&B.sd_rows[set], rows, st));
+      TRY(M.alloc(&B.sd_nnz[set], n_sd, true, st));
+      launch_count_sd_nnz(set == 0 ? S.tP_I : S.tP_all, set == 0 ? A_II.e64() : Hp.e64(),
+                          B.sd_nnz[set], st);
+    }
+  }
   TRY(M.alloc(&B.cs.done, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.part1, (size_t)mt * kp, true, st));
   TRY(M.alloc(&B.cs.part2, (size_t)mt * kp, true, st));
@@ -912,7 +885,27 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
                      cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   for (auto& s : Bo.h_sigma) s = std::sqrt(std::max(s, 0.0));
-  if (g_prof.on) g_prof.collect();
+  if (g_prof.on) {
+    g_prof.collect();
+    // algorithmic bytes of the work the CG kernels actually did (converged subdomains
+    // and column packs are skipped): sparse product = stored entries (value + index)
+    // of the active subdomains + read p and write q per open (row, 16-byte pack); x/r
+    // update = read x, r, p, q and write x, r per open (row, pack); p update = read r,
+    // p and write p per open (row, pack); coarse = E^{-1} entries read.  Diagonal,
+    // aggregate-index and y_c reads are not counted.
+    std::vector<unsigned long long> wt((size_t)4 * n_sd);
+    CK(cudaMemcpy(wt.data(), B.cs.work, wt.size() * sizeof(unsigned long long),
+                  cudaMemcpyDeviceToHost));
+    double w[4] = {0, 0, 0, 0};
+    for (int k2 = 0; k2 < 4; ++k2)
+      for (int i = 0; i < n_sd; ++i) w[k2] += (double)wt[(size_t)k2 * n_sd + i];
+    const double tsz = B.mixed ? 4.0 : 8.0;
+    const int wide = B.mixed ? 0 : 1;
+    g_prof.bytes[0 + wide] += w[0] * (tsz + 4.0) + w[1] * 16.0 * 2.0;
+    g_prof.bytes[2 + wide] += w[1] * 16.0 * 6.0;
+    g_prof.bytes[4 + wide] += w[2] * 16.0 * 3.0;
+    g_prof.bytes[6 + wide] += w[3] * tsz;
+  }
   Bo.stats[0] = B.iters[0];
   Bo.stats[1] = B.iters[1];
   Bo.stats[2] = B.iters[2];

@@ -79,6 +79,14 @@ struct CgState {
   int* counter;                     // n_sd
   int* iters;                       // n_sd
   int* active;                      // n_sd: active columns after the last update
+  // work counters of the algorithmic-bytes model, kept by the coarse kernel (once per
+  // subdomain and step; null: not counted): work[k * n_sd + sd] with k = [0] stored
+  // entries read by the sparse product, [1] (row, open pack) pairs of the sparse
+  // product and the x/r update, [2] those of the p update, [3] E^{-1} entries read.
+  // sd_rows / sd_nnz: rows and stored entries of each subdomain for the current solve.
+  unsigned long long* work;
+  const int32_t* sd_rows;
+  const int64_t* sd_nnz;
 };
 
 // Coarse level of the two-level additive preconditioner M^{-1} = D^{-1} + Z E^{-1} Z^T
@@ -159,6 +167,9 @@ void launch_residual64(const DTiles& tiles, const EllView<double>& A, const doub
                        const double* x64, double* r64, int kp, int nc, int ncn, double rtol2,
                        int first, bool floor_ref, const double* anorm, const RefineState& s,
                        cudaStream_t st);
+// out[sd] += stored entries in the rows of the tiles of sd (out zeroed by the caller)
+void launch_count_sd_nnz(const DTiles& tiles, const EllView<double>& A, int64_t* out,
+                         cudaStream_t st);
 // anorm[sd] = max over the rows of tiles in sd of sum_j |a_ij| (anorm zeroed by caller)
 void launch_row_abs_max(const DTiles& tiles, const EllView<double>& A, double* anorm,
                         cudaStream_t st);

@@ -129,6 +129,18 @@ __device__ void sd_colsums(const Geo& g, const double* part, int kp, int lo, int
   __syncthreads();
 }
 
+// the N columns of pack tx of subdomain sd have all converged (their work can be skipped:
+// converged columns have alpha = 0 and are reset at the next residual replacement)
+template <typename T>
+__device__ __forceinline__ bool pack_done(const CgState& s, int sd, int kp, int tx) {
+  constexpr int N = Pack<T>::N;
+  const int* d = s.done + sd * kp + tx * N;
+  bool all = true;
+#pragma unroll
+  for (int e = 0; e < N; ++e) all = all && d[e] != 0;
+  return all;
+}
+
 __device__ __forceinline__ void count_active(const Geo& g, const int* done, int sd, int kp,
                                              int* active) {
   __shared__ int cnt;
@@ -268,13 +280,15 @@ __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, A.W);
   const int tile = blockIdx.x, sd = tl.sd[tile];
+  if (s.active[sd] == 0) return;  // every column of this subdomain has converged
   const int r0 = tl.r0[tile], r1 = tl.r1[tile];
   stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
   __syncthreads();
   T acc[N];
 #pragma unroll
   for (int e = 0; e < N; ++e) acc[e] = T(0);
-  for (int rr = g.ty; rr < r1 - r0; rr += g.rb) {
+  const int rend = pack_done<T>(s, sd, kp, g.tx) ? 0 : r1 - r0;
+  for (int rr = g.ty; rr < rend; rr += g.rb) {
     int64_t row = r0 + rr;
     Pack<T> qv = spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, p, kp);
     int64_t o = row * kp + g.tx * N;
@@ -537,6 +551,7 @@ __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
   int tile = blockIdx.x, sd = tl.sd[tile];
+  if (s.active[sd] == 0) return;
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
   const bool coarse = co.aloc != nullptr;
   T* cs = slot_smem<T>(g, kp);
@@ -548,13 +563,14 @@ __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
     __syncthreads();
   }
   RestrictAcc<T> ra;
+  const int64_t rend = pack_done<T>(s, sd, kp, g.tx) ? r0 : r1;
   T al[N];
 #pragma unroll
   for (int e = 0; e < N; ++e) al[e] = (T)s.alpha[sd * kp + g.tx * N + e];
   T arr[N], arz[N];
 #pragma unroll
   for (int e = 0; e < N; ++e) arr[e] = arz[e] = T(0);
-  for (int64_t row = r0 + g.ty; row < r1; row += g.rb) {
+  for (int64_t row = r0 + g.ty; row < rend; row += g.rb) {
     int64_t o = row * kp + g.tx * N;
     Pack<T> xv = ld(x + o), rv = ld(r + o), pv = ld(p + o), qv = ld(q + o);
     T d = dinv[row];
@@ -604,13 +620,26 @@ __global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s,
   double* red = reinterpret_cast<double*>(raw + align16(sizeof(T) * kMaxAgg * CW));
   __shared__ double cd[CW];
   const int sd = blockIdx.x, c0 = blockIdx.y * CW;
-  const int n = co.aloc ? co.nca[sd] : 0;
+  if (s.active[sd] == 0) return;
+  // a chunk whose columns have all converged needs no coarse product
+  bool chunk_open = false;
+  for (int j = 0; j < CW && c0 + j < kp; ++j) chunk_open = chunk_open || !s.done[sd * kp + c0 + j];
+  const int n = (co.aloc && chunk_open) ? co.nca[sd] : 0;
+  // open packs of this chunk before the update (the sparse product and the x/r update
+  // of this step worked on them)
+  constexpr int PN = Pack<T>::N;
+  int open_pre = 0;
+  if (s.work && mode == kCoarseStep && g.tid == 0)
+    for (int j = 0; j < CW && c0 + j < kp; j += PN) {
+      bool open = false;
+      for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + c0 + j + e];
+      open_pre += open;
+    }
   const int a0 = n ? co.aoff[sd] : 0;
   // r_c = Z^T r: thread a sums the partial rows of aggregate a over the tiles holding
   // it (contiguous 16-byte packs of this column chunk; kp and c0 are multiples of the
   // pack width).  Rows n .. round_up(n, 8) are zero: the product below runs in steps
   // of 8.
-  constexpr int PN = Pack<T>::N;
   const int n8 = (n + 7) & ~7;
   for (int a = g.tid; a < n8; a += g.nth) {
     T v[CW];
@@ -697,6 +726,24 @@ __global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s,
     }
   }
   if (mode != kCoarseStep) return;
+  if (s.work) {
+    __syncthreads();
+    if (g.tid == 0) {
+      // open packs after the update (the p update works on them), and the work counts
+      int open_post = 0;
+      for (int j = 0; j < CW && c0 + j < kp; j += PN) {
+        bool open = false;
+        for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + c0 + j + e];
+        open_post += open;
+      }
+      const int nsd = tl.n_sd;
+      const unsigned long long rows = (unsigned long long)s.sd_rows[sd];
+      if (blockIdx.y == 0) atomicAdd(s.work + sd, (unsigned long long)s.sd_nnz[sd]);
+      atomicAdd(s.work + nsd + sd, (unsigned long long)open_pre * rows);
+      atomicAdd(s.work + 2 * nsd + sd, (unsigned long long)open_post * rows);
+      if (n > 0) atomicAdd(s.work + 3 * nsd + sd, (unsigned long long)n * n);
+    }
+  }
   if (!last_block(g, s.counter, sd, gridDim.y)) return;
   count_active(g, s.done, sd, kp, s.active);
   if (g.tid == 0 && s.active[sd] > 0) s.iters[sd] += 1;
@@ -711,7 +758,9 @@ __global__ void k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p,
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
   int tile = blockIdx.x, sd = tl.sd[tile];
+  if (s.active[sd] == 0) return;
   int r0 = tl.r0[tile], r1 = tl.r1[tile];
+  const int64_t rend = pack_done<T>(s, sd, kp, g.tx) ? r0 : r1;
   const bool coarse = co.aloc != nullptr;
   const int64_t a0 = coarse ? co.aoff[sd] : 0;
   T be[N], ga[N];
@@ -725,7 +774,7 @@ __global__ void k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p,
   T apr[N];
 #pragma unroll
   for (int e = 0; e < N; ++e) apr[e] = T(0);
-  for (int64_t row = r0 + g.ty; row < r1; row += g.rb) {
+  for (int64_t row = r0 + g.ty; row < rend; row += g.rb) {
     int64_t o = row * kp + g.tx * N;
     Pack<T> rv = ld(r + o), pv, yv;
     if (needp) pv = ld(p + o);
@@ -1034,6 +1083,26 @@ void launch_accum_reset(const DTiles& tiles, T* xT, double* x64, int kp, cudaStr
   if (tiles.n <= 0) return;
   count_launch();
   k_accum_reset<T><<<tiles.n, dim3(32, 8), 0, st>>>(tiles, xT, x64, kp);
+}
+
+// out[sd] += stored entries of the rows of each tile of sd (one thread per row)
+__global__ void k_count_sd_nnz(DTiles tl, EllView<double> A, unsigned long long* out) {
+  const int tile = blockIdx.x, sd = tl.sd[tile];
+  const int64_t row = tl.r0[tile] + (int64_t)threadIdx.x;
+  unsigned long long c = 0;
+  if (row < tl.r1[tile]) {
+    const int w = A.width[row >> 5];
+    for (int j = 0; j < w; ++j) c += A.col[ell_at(row, j, A.W)] >= 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out + sd, c);
+}
+
+void launch_count_sd_nnz(const DTiles& tiles, const EllView<double>& A, int64_t* out,
+                         cudaStream_t st) {
+  if (tiles.n <= 0) return;
+  count_launch();
+  k_count_sd_nnz<<<tiles.n, kTileRows, 0, st>>>(tiles, A, (unsigned long long*)out);
 }
 
 void launch_row_abs_max(const DTiles& tiles, const EllView<double>& A, double* out,
