@@ -583,7 +583,6 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   const int64_t nEllP = ceil_div(nP, 32) * 32 * WP;
   const int64_t nEllW = ceil_div(nW, 32) * 32 * WW;
   const int64_t nEllO = ceil_div(nO, 32) * 32 * WW;
-  const int64_t nIncP = (int64_t)hp.incP_tet.size();
 
   CK(cudaMallocHost((void**)&B.h_poll, 2 * sizeof(int)));
   TRY(M.alloc(&B.d_poll, 2, true, st));
@@ -739,6 +738,9 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.alloc(&B.cs.rzf, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.gam, (size_t)n_sd * kp, true, st));
   TRY(M.alloc(&B.cs.pr, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.alpha32, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.beta32, (size_t)n_sd * kp, true, st));
+  TRY(M.alloc(&B.cs.gam32, (size_t)n_sd * kp, true, st));
   if (g_prof.on) {
     // work counters and, per matrix set, rows and stored entries of every subdomain
     TRY(M.alloc(&B.cs.work, (size_t)4 * n_sd, true, st));
@@ -817,14 +819,14 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   const double rt_sketch = o.sketch_rtol > 0.0 ? o.sketch_rtol : o.cg_rtol;
 
   // ---- sketch: W = ((H^+)^{-1} L xi)_B ----
-  double* lrow;
-  TRY(M.alloc(&lrow, nIncP * 4, false, st));
-  launch_elem_lrow(nIncP, S.incP_tet, S.incP_code, S.xyz, S.tets, lrow, st);
+  float2* lsplit;
+  TRY(M.alloc(&lsplit, (size_t)hp.n_tets * 10, false, st));
+  launch_elem_chol(hp.n_tets, S.xyz, S.tets, lsplit, st);
   int32_t *d_ksd, *d_msd, *d_msel;
   TRY(M.upload(&d_ksd, h_k, st));
   TRY(M.upload(&d_msd, h_rank, st));
   TRY(M.alloc(&d_msel, n_sd, true, st));
-  launch_sketch_rhs(0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lrow, k, o.seed,
+  launch_sketch_rhs(0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lsplit, k, o.seed,
                     vS, kp, st, d_ksd);
   TRY(solve(S.tP_all, Hp, false, vS, vG, k, 0, rt_sketch));
 
@@ -1109,14 +1111,14 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, i
   cudaStream_t st = (cudaStream_t)stream;
   int k = opts->rank + opts->oversample;
   int64_t row0 = hp.Poff[sub], n_rows = hp.Poff[sub + 1] - row0;
-  int64_t nInc = (int64_t)hp.incP_tet.size();
   Allocs A;
-  double *lrow, *res;
-  TRY(A.alloc(&lrow, nInc * 4, false, st));
+  float2* lsplit;
+  double* res;
+  TRY(A.alloc(&lsplit, (size_t)hp.n_tets * 10, false, st));
   TRY(A.alloc(&res, (hp.nP) * (size_t)k, true, st));
-  launch_elem_lrow(nInc, sd->incP_tet, sd->incP_code, sd->xyz, sd->tets, lrow, st);
-  launch_sketch_rhs(row0, n_rows, sd->p_sd, sd->incP_ptr,
-                    sd->incP_tet, sd->incP_code, lrow, k, opts->seed, res, k, st, nullptr);
+  launch_elem_chol(hp.n_tets, sd->xyz, sd->tets, lsplit, st);
+  launch_sketch_rhs(row0, n_rows, sd->p_sd, sd->incP_ptr, sd->incP_tet, sd->incP_code, lsplit,
+                    k, opts->seed, res, k, st, nullptr);
   CK(cudaGetLastError());
   std::vector<double> tmp((size_t)n_rows * k);
   CK(cudaMemcpyAsync(tmp.data(), res + row0 * k, tmp.size() * sizeof(double),

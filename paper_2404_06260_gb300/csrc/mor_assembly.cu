@@ -48,17 +48,16 @@ void launch_assemble(int64_t n_rows, const int64_t* inc_ptr, const int32_t* inc_
       n_rows, inc_ptr, inc_tet, inc_code, W, xyz, tets, kappa, valA, valH, load, err);
 }
 
-// element H1 matrix and its 4x4 Cholesky factor; row a of L into lrow[4q..4q+3]
-__global__ void k_elem_lrow(int64_t n_inc, const int32_t* __restrict__ inc_tet,
-                            const uint32_t* __restrict__ inc_code,
-                            const double* __restrict__ xyz, const int32_t* __restrict__ tets,
-                            double* __restrict__ lrow) {
-  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= n_inc) return;
-  int32_t t = inc_tet[q];
-  int a = inc_code[q] & 3u;
+// element H1 matrix H_T = |T| grad.grad + |T|(1 + d_ab)/20 and its lower Cholesky factor
+// L_T (H_T = L_T L_T^T), once per element: the 10 entries L[a][b], b <= a, at
+// a(a+1)/2 + b, each split into binary32 hi + lo (hi = fl32(L), lo = fl32(L - hi)), so
+// the sketch sums can run in double-binary32 arithmetic
+__global__ void k_elem_chol(int64_t n_tets, const double* __restrict__ xyz,
+                            const int32_t* __restrict__ tets, float2* __restrict__ lsplit) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_tets) return;
   double G[4][3], vol;
-  tet_gradients(xyz, tets, t, G, vol);
+  tet_gradients(xyz, tets, (int32_t)t, G, vol);
   double H[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -80,25 +79,40 @@ __global__ void k_elem_lrow(int64_t n_inc, const int32_t* __restrict__ inc_tet,
     }
   }
 #pragma unroll
-  for (int b = 0; b < 4; ++b) lrow[4 * q + b] = (b <= a) ? L[a][b] : 0.0;
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      float hi = (float)L[a][b];
+      float lo = (float)(L[a][b] - (double)hi);
+      lsplit[10 * t + a * (a + 1) / 2 + b] = make_float2(hi, lo);
+    }
 }
 
-void launch_elem_lrow(int64_t n_inc, const int32_t* inc_tet, const uint32_t* inc_code,
-                      const double* xyz, const int32_t* tets, double* lrow, cudaStream_t st) {
-  if (n_inc <= 0) return;
+void launch_elem_chol(int64_t n_tets, const double* xyz, const int32_t* tets, float2* lsplit,
+                      cudaStream_t st) {
+  if (n_tets <= 0) return;
   int bs = 256;
   count_launch();
-  k_elem_lrow<<<(unsigned)((n_inc + bs - 1) / bs), bs, 0, st>>>(n_inc, inc_tet, inc_code,
-                                                                 xyz, tets, lrow);
+  k_elem_chol<<<(unsigned)((n_tets + bs - 1) / bs), bs, 0, st>>>(n_tets, xyz, tets, lsplit);
 }
 
-// one warp per row, lanes over columns.  The Gaussian draws are binary32 (bit-exact
-// Box-Muller); the sums over element incidences are binary64 whatever the solve
-// precision, so every precision sketches with the same test matrix W
+// (hi, lo) += x, the rounding error of hi + x kept in lo (Knuth's two-sum)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  float s = hi + x;
+  float bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
+// one warp per row, lanes over columns: out[r, j] = sum over incident elements T of
+// (L_T xi_T[:, j])[a(r)].  The Gaussian draws are binary32 (bit-exact Box-Muller); the
+// products and sums run in double-binary32 arithmetic (about 2^-48 relative), the same in
+// every solve precision, so every precision sketches with the same test matrix W
 __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __restrict__ row_sd,
                              const int64_t* __restrict__ inc_ptr,
                              const int32_t* __restrict__ inc_tet,
-                             const double* __restrict__ lrow, int k, uint64_t seed,
+                             const uint32_t* __restrict__ inc_code,
+                             const float2* __restrict__ lsplit, int k, uint64_t seed,
                              double* __restrict__ out, int ld,
                              const int32_t* __restrict__ k_sd) {
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -110,29 +124,35 @@ __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __rest
   const int kk = k_sd ? min(k, (int)k_sd[sd]) : k;
   for (int j = lane + kk; j < k; j += 32) out[r * ld + j] = 0.0;
   for (int j = lane; j < kk; j += 32) {
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     for (int64_t q = q0; q < q1; ++q) {
       float z[4];
-      field_normals((uint32_t)inc_tet[q], (uint32_t)j, sd, seed, z);
-      const double* L = lrow + 4 * q;
-      acc += L[0] * (double)z[0] + L[1] * (double)z[1] + L[2] * (double)z[2] +
-             L[3] * (double)z[3];
+      const uint32_t t = (uint32_t)inc_tet[q];
+      field_normals(t, (uint32_t)j, sd, seed, z);
+      const int a = inc_code[q] & 3u;
+      const float2* La = lsplit + 10 * (int64_t)t + a * (a + 1) / 2;
+      for (int b = 0; b <= a; ++b) {
+        const float2 l = La[b];
+        const float p = l.x * z[b];
+        const float e = fmaf(l.x, z[b], -p);  // l.x z[b] = p + e exactly
+        df_add(hi, lo, p);
+        lo += e + l.y * z[b];
+      }
     }
-    out[r * ld + j] = acc;
+    out[r * ld + j] = (double)hi + (double)lo;
   }
 }
 
 void launch_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int64_t* inc_ptr, const int32_t* inc_tet,
-                       const uint32_t* inc_code, const double* lrow, int k, uint64_t seed,
+                       const uint32_t* inc_code, const float2* lsplit, int k, uint64_t seed,
                        double* out, int ld, cudaStream_t st, const int32_t* k_sd) {
-  (void)inc_code;
   if (n_rows <= 0) return;
   int bs = 256;
   unsigned grid = (unsigned)((n_rows * 32 + bs - 1) / bs);
   count_launch();
-  k_sketch_rhs<<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, lrow, k, seed, out,
-                                    ld, k_sd);
+  k_sketch_rhs<<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, inc_code, lsplit,
+                                    k, seed, out, ld, k_sd);
 }
 
 // one thread per destination row; warps cover whole slices so the slice width is a

@@ -77,7 +77,10 @@ __global__ void __launch_bounds__(kGramThreads)
 
 // cyclic Jacobi with the round-robin (circle) ordering: m/2 disjoint rotations per
 // round, m-1 rounds per sweep; A <- J^T A J, V <- V J with the symmetric 2x2 Schur
-// rotation (Golub & Van Loan, Alg. 8.4.1)
+// rotation (Golub & Van Loan, Alg. 8.4.1).  A pair is rotated only while
+// |a_pq| > eps sqrt(|a_pp a_qq|) (eps = 2^-52), the threshold that keeps small
+// eigenvalues accurate relative to themselves (Demmel & Veselic); the iteration stops
+// after a sweep without rotations (at most 40 sweeps).
 __global__ void k_sym_eig(const double* __restrict__ A, int ld, int n, double* evals,
                           double* evecs) {
   extern __shared__ double sh[];
@@ -110,20 +113,11 @@ __global__ void k_sym_eig(const double* __restrict__ A, int ld, int n, double* e
     __syncthreads();
     return r;
   };
-  double f2 = 0.0;
-  for (int idx = tid; idx < m * m; idx += nth) {
-    double x = a[(idx / m) * lds + idx % m];
-    f2 += x * x;
-  }
-  double fro2 = block_sum(f2);
+  (void)block_sum;
+  __shared__ int nrot;
   for (int sweep = 0; sweep < 40 && m > 1; ++sweep) {
-    double o2 = 0.0;
-    for (int idx = tid; idx < m * m; idx += nth) {
-      int i = idx / m, j = idx % m;
-      if (i != j) o2 += a[i * lds + j] * a[i * lds + j];
-    }
-    double off2 = block_sum(o2);
-    if (!(off2 > 1e-32 * fro2)) break;
+    if (tid == 0) nrot = 0;
+    __syncthreads();
     for (int round = 0; round < m - 1; ++round) {
       for (int k = tid; k < m / 2; k += nth) {
         int x0 = k, x1 = m - 1 - k;
@@ -131,7 +125,8 @@ __global__ void k_sym_eig(const double* __restrict__ A, int ld, int n, double* e
         int q = ((x1 - 1 + round) % (m - 1)) + 1;
         double apq = a[p * lds + q];
         double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
+        if (fabs(apq) > 0x1p-52 * sqrt(fabs(a[p * lds + p] * a[q * lds + q]))) {
+          atomicAdd(&nrot, 1);
           double tau = (a[q * lds + q] - a[p * lds + p]) / (2.0 * apq);
           double t;
           if (fabs(tau) > 1e150)
@@ -149,8 +144,9 @@ __global__ void k_sym_eig(const double* __restrict__ A, int ld, int n, double* e
       __syncthreads();
       for (int w = tid; w < (m / 2) * m; w += nth) {
         int k = w / m, j = w % m;
-        int p = rp[k], q = rq[k];
         double c = rc[k], s = rs[k];
+        if (s == 0.0) continue;  // pair not rotated
+        int p = rp[k], q = rq[k];
         double ap = a[p * lds + j], aq = a[q * lds + j];
         a[p * lds + j] = c * ap - s * aq;
         a[q * lds + j] = s * ap + c * aq;
@@ -158,8 +154,9 @@ __global__ void k_sym_eig(const double* __restrict__ A, int ld, int n, double* e
       __syncthreads();
       for (int w = tid; w < (m / 2) * m; w += nth) {
         int k = w / m, i = w % m;
-        int p = rp[k], q = rq[k];
         double c = rc[k], s = rs[k];
+        if (s == 0.0) continue;
+        int p = rp[k], q = rq[k];
         double ap = a[i * lds + p], aq = a[i * lds + q];
         a[i * lds + p] = c * ap - s * aq;
         a[i * lds + q] = s * ap + c * aq;
@@ -169,6 +166,10 @@ __global__ void k_sym_eig(const double* __restrict__ A, int ld, int n, double* e
       }
       __syncthreads();
     }
+    // every thread reads the count before thread 0 resets it for the next sweep
+    const int rotated = nrot;
+    __syncthreads();
+    if (rotated == 0) break;
   }
   double* ev = evals + (int64_t)sd * ld;
   double* V = evecs + (int64_t)sd * ld * ld;

@@ -28,17 +28,18 @@ void launch_assemble(int64_t n_rows, const int64_t* inc_ptr, const int32_t* inc_
                      const double* kappa, double* valA, double* valH, double* load,
                      int* err, cudaStream_t st);
 
-// Row a of the lower Cholesky factor of the element H1 matrix, for every incidence
-// entry (the element factors L_T of the field sketch, L L^T = H^+).
-void launch_elem_lrow(int64_t n_inc, const int32_t* inc_tet, const uint32_t* inc_code,
-                      const double* xyz, const int32_t* tets, double* lrow, cudaStream_t st);
+// Lower Cholesky factor L_T of every element's H1 matrix (the element factors of the
+// field sketch, L L^T = H^+): lsplit[10 t + a(a+1)/2 + b] = L[a][b] (b <= a) as binary32
+// hi + lo.
+void launch_elem_chol(int64_t n_tets, const double* xyz, const int32_t* tets, float2* lsplit,
+                      cudaStream_t st);
 
 // out[r, j] = sum over incident elements T of (L_T xi_T[:, j])[a(r)], j < k_sd[row_sd[r]]
 // (or j < k when k_sd is null), zero for the other j < k, for rows [row0, row0 + n_rows);
-// xi from Philox counter (T, j, row_sd[r], 0), summed in binary64.
+// xi from Philox counter (T, j, row_sd[r], 0); products and sums in double-binary32.
 void launch_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int64_t* inc_ptr, const int32_t* inc_tet,
-                       const uint32_t* inc_code, const double* lrow, int k, uint64_t seed,
+                       const uint32_t* inc_code, const float2* lsplit, int k, uint64_t seed,
                        double* out, int ld, cudaStream_t st, const int32_t* k_sd);
 
 // Extract a sliced-ELL matrix from an assembled pattern: destination row r takes source
@@ -74,6 +75,8 @@ struct CgState {
   double* gam;                      // n_sd x kp: p = gam z + beta p in the p update
   double* pr;                       // n_sd x kp: p.r after the p update (the step length
                                     // is the exact line search alpha = p.r / p.Ap)
+  float *alpha32, *beta32, *gam32;  // n_sd x kp: binary32 copies written beside alpha,
+                                    // beta, gam (binary32 kernels load them as packs)
   int* done;                        // n_sd x kp
   double *part1, *part2;            // n_tiles x kp
   int* counter;                     // n_sd

@@ -129,6 +129,23 @@ __device__ void sd_colsums(const Geo& g, const double* part, int kp, int lo, int
   __syncthreads();
 }
 
+// CG coefficients: binary64 state with a binary32 copy
+__device__ __forceinline__ void set_coef(double* c64, float* c32, int i, double v) {
+  c64[i] = v;
+  c32[i] = (float)v;
+}
+// the N coefficients of pack tx of subdomain sd in the working precision
+template <typename T>
+__device__ __forceinline__ Pack<T> coef_pack(const double* c64, const float* c32, int sd,
+                                             int kp, int tx) {
+  constexpr int N = Pack<T>::N;
+  if constexpr (sizeof(T) == 4) {
+    return ld(reinterpret_cast<const T*>(c32) + sd * kp + tx * N);
+  } else {
+    return ld(reinterpret_cast<const T*>(c64) + sd * kp + tx * N);
+  }
+}
+
 // the N columns of pack tx of subdomain sd have all converged (their work can be skipped:
 // converged columns have alpha = 0 and are reset at the next residual replacement)
 template <typename T>
@@ -313,7 +330,7 @@ __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
       else
         s.done[i] = 1;  // breakdown (p = 0 or indefinite): stop this column
     }
-    s.alpha[i] = a;
+    set_coef(s.alpha, s.alpha32, i, a);
   }
 }
 
@@ -532,9 +549,9 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r,
     s.bb[i] = (c < ncn) ? bref : bb;
     s.rr[i] = bb;
     s.done[i] = (c >= nc || !(bb > 0.0)) ? 1 : 0;
-    s.alpha[i] = 0.0;
-    s.beta[i] = 0.0;
-    s.gam[i] = 1.0;
+    set_coef(s.alpha, s.alpha32, i, 0.0);
+    set_coef(s.beta, s.beta32, i, 0.0);
+    set_coef(s.gam, s.gam32, i, 1.0);
   }
   if (g.tid == 0) s.iters[sd] = 0;
   __syncthreads();
@@ -564,9 +581,10 @@ __global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
   }
   RestrictAcc<T> ra;
   const int64_t rend = pack_done<T>(s, sd, kp, g.tx) ? r0 : r1;
+  const Pack<T> alp = coef_pack<T>(s.alpha, s.alpha32, sd, kp, g.tx);
   T al[N];
 #pragma unroll
-  for (int e = 0; e < N; ++e) al[e] = (T)s.alpha[sd * kp + g.tx * N + e];
+  for (int e = 0; e < N; ++e) al[e] = alp.v[e];
   T arr[N], arz[N];
 #pragma unroll
   for (int e = 0; e < N; ++e) arr[e] = arz[e] = T(0);
@@ -719,8 +737,8 @@ __global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s,
           s.rz[i] = rzn;
         }
       }
-      s.beta[i] = be;
-      s.gam[i] = 1.0;
+      set_coef(s.beta, s.beta32, i, be);
+      set_coef(s.gam, s.gam32, i, 1.0);
     } else {
       s.rz[i] = rzn;
     }
@@ -763,12 +781,14 @@ __global__ void k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p,
   const int64_t rend = pack_done<T>(s, sd, kp, g.tx) ? r0 : r1;
   const bool coarse = co.aloc != nullptr;
   const int64_t a0 = coarse ? co.aoff[sd] : 0;
+  const Pack<T> bep = coef_pack<T>(s.beta, s.beta32, sd, kp, g.tx);
+  const Pack<T> gap = coef_pack<T>(s.gam, s.gam32, sd, kp, g.tx);
   T be[N], ga[N];
   bool needp = false;
 #pragma unroll
   for (int e = 0; e < N; ++e) {
-    be[e] = (T)s.beta[sd * kp + g.tx * N + e];
-    ga[e] = (T)s.gam[sd * kp + g.tx * N + e];
+    be[e] = bep.v[e];
+    ga[e] = gap.v[e];
     needp = needp || be[e] != T(0);
   }
   T apr[N];
@@ -885,9 +905,9 @@ __global__ void k_cg_replace(DTiles tl, const double* __restrict__ r64, T* __res
     s.rzf[i] = sm.sums[c];
     s.bb[i] = rs.obb[i];
     s.done[i] = done ? 1 : 0;
-    s.alpha[i] = 0.0;
-    s.beta[i] = (done || restart) ? 0.0 : 1.0;
-    s.gam[i] = (done || restart) ? 1.0 : 0.0;
+    set_coef(s.alpha, s.alpha32, i, 0.0);
+    set_coef(s.beta, s.beta32, i, (done || restart) ? 0.0 : 1.0);
+    set_coef(s.gam, s.gam32, i, (done || restart) ? 1.0 : 0.0);
   }
   __syncthreads();
   count_active(g, s.done, sd, kp, s.active);
