@@ -133,11 +133,15 @@ typedef struct {
                           Morton-ordered rows of a subdomain, at most 256 per
                           subdomain) and E = Z^T A Z inverted per subdomain; 0: Jacobi
                           only.  Changes iteration counts, not the solutions.         */
+  int32_t h1_weighted; /* 0: the H1 inner product of H_i and H^+ is the unweighted
+                          int grad w . grad v + w v of Sec. 4 (as printed); 1: its
+                          gradient part is weighted by the coefficient k, a variant for
+                          high contrast (the paper analyses k = 1, Sec. 7.3)           */
 } mor_basis_opts;
 
 /* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
  * max_iter 20000, replace_every 40, normwise 1, drift_restart 1.5, sketch_rtol 0,
- * tau 1e-12, orth_tol 1e-14, coarse_rows 100). */
+ * tau 1e-12, orth_tol 1e-14, coarse_rows 100, h1_weighted 0). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 
 /* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (24)):

@@ -35,7 +35,10 @@ from . import fem
 from .rng import field_normals, node_normals
 
 
-def local_system(mesh, kappa, s, f=None):
+def local_system(mesh, kappa, s, f=None, h1_weighted=False):
+    """h1_weighted: the H1 forms H^+ and H_i weight their gradient part by the
+    coefficient, int k grad w . grad v + w v, instead of the unweighted form of Sec. 4
+    (a variant for high-contrast k; the paper analyses k = 1 only, Sec. 7.3)."""
     n = mesh.n_nodes
     I, B, omega, owned = s["I"], s["B"], s["omega"], s["owned"]
     nI, nB = len(I), len(B)
@@ -45,7 +48,8 @@ def local_system(mesh, kappa, s, f=None):
     Tp = mesh.tets[s["plus_tets"]]
     G, vol = fem.tet_geometry(mesh.xyz, Tp)
     Kp = fem.stiffness_elements(G, vol, kappa[s["plus_tets"]])
-    Hp = fem.stiffness_elements(G, vol) + fem.mass_elements(vol)
+    wp = kappa[s["plus_tets"]] if h1_weighted else None
+    Hp = fem.stiffness_elements(G, vol, wp) + fem.mass_elements(vol)
     A_plus = fem.assemble_matrix(Tp, Kp, pmap, nI + nB)
     H_plus = fem.assemble_matrix(Tp, Hp, pmap, nI + nB)
     fe = fem.load_unit(vol) if f is None else fem.load_function(mesh.xyz, Tp, vol, f)
@@ -55,7 +59,8 @@ def local_system(mesh, kappa, s, f=None):
     Go, volo = fem.tet_geometry(mesh.xyz, To)
     wmap = -np.ones(n, dtype=np.int64)
     wmap[omega] = np.arange(len(omega))
-    H_i = fem.assemble_matrix(To, fem.stiffness_elements(Go, volo) + fem.mass_elements(volo),
+    wo = kappa[s["omega_tets"]] if h1_weighted else None
+    H_i = fem.assemble_matrix(To, fem.stiffness_elements(Go, volo, wo) + fem.mass_elements(volo),
                               wmap, len(omega))
     omap = -np.ones(n, dtype=np.int64)
     omap[owned] = np.arange(len(owned))
@@ -69,7 +74,7 @@ def local_system(mesh, kappa, s, f=None):
     D = sp.csr_matrix((np.ones(len(owned)), (np.arange(len(owned)), wmap[owned])),
                       shape=(len(owned), len(omega)))
     A_plus = A_plus.tocsr()
-    return dict(nI=nI, nB=nB, pmap=pmap, A_plus=A_plus, H_plus=H_plus.tocsr(),
+    return dict(nI=nI, nB=nB, pmap=pmap, A_plus=A_plus, H_plus=H_plus.tocsr(), h1_w=wp,
                 A_II=A_plus[:nI, :nI].tocsc(), A_IB=A_plus[:nI, nI:].tocsr(),
                 b_I=b_plus[:nI], H_i=H_i, A_PP=A_PP, b_P=b_P, C=C, D=D)
 
@@ -100,7 +105,7 @@ def field_sketch_rhs(mesh, s, loc, k, seed):
     T_ids = s["plus_tets"]
     Tp = mesh.tets[T_ids]
     G, vol = fem.tet_geometry(mesh.xyz, Tp)
-    He = fem.stiffness_elements(G, vol) + fem.mass_elements(vol)
+    He = fem.stiffness_elements(G, vol, loc.get("h1_w")) + fem.mass_elements(vol)
     Le = np.linalg.cholesky(He)                          # (t, 4, 4) lower
     xi = field_normals(seed, s["i"], T_ids, k).astype(np.float64)   # (t, 4, k)
     nt = len(T_ids)
@@ -126,8 +131,9 @@ def sketch_W(mesh, s, loc, k, seed, mode, R_BB=None):
 
 
 def local_basis(mesh, kappa, s, rank, oversample=0, seed=0, sketch="field",
-                explicit=False, eps=None, tau=1e-12, f=None, keep_all=False):
-    loc = local_system(mesh, kappa, s, f)
+                explicit=False, eps=None, tau=1e-12, f=None, keep_all=False,
+                h1_weighted=False):
+    loc = local_system(mesh, kappa, s, f, h1_weighted)
     C, D = loc["C"], loc["D"]
     luA = splu(loc["A_II"])
     u0 = luA.solve(loc["b_I"])

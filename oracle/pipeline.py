@@ -14,11 +14,12 @@ from .subdomains import all_subdomains
 
 def run(mesh, kappa, owner, rank, oversample, r_hops, seed, sketch="field",
         explicit=False, eps=None, tau=1e-12, f=None, keep_all=False, fe_solution=True,
-        interface=True):
+        interface=True, h1_weighted=False):
     subs = all_subdomains(mesh, owner, r_hops)
     ranks = np.broadcast_to(np.asarray(rank), (len(subs),))   # per-subdomain m_i
     bases = [local_basis(mesh, kappa, s, int(ranks[j]), oversample, seed, sketch=sketch,
-                         explicit=explicit, eps=eps, tau=tau, f=f, keep_all=keep_all)
+                         explicit=explicit, eps=eps, tau=tau, f=f, keep_all=keep_all,
+                         h1_weighted=h1_weighted)
              for j, s in enumerate(subs)]
     out = dict(subs=subs, bases=bases)
     if interface:

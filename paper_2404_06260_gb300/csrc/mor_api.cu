@@ -358,6 +358,7 @@ int mor_basis_opts_default(mor_basis_opts* o) {
   o->tau = 1e-12;
   o->orth_tol = 1e-14;
   o->coarse_rows = 100;
+  o->h1_weighted = 0;
   return MOR_OK;
 }
 
@@ -597,9 +598,11 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.alloc(&valA_W, nEllW, true, st));
   TRY(M.alloc(&valH_W, nEllW, true, st));
   TRY(M.alloc(&loadW, nW, true, st));
-  launch_assemble(nP, S.incP_ptr, S.incP_tet, S.incP_code, WP, S.xyz, S.tets, S.kappa, valA_P,
+  launch_assemble(nP, S.incP_ptr, S.incP_tet, S.incP_code, WP, S.xyz, S.tets, S.kappa,
+                  o.h1_weighted, valA_P,
                   valH_P, loadP, d_err, st);
-  launch_assemble(nW, S.incW_ptr, S.incW_tet, S.incW_code, WW, S.xyz, S.tets, S.kappa, valA_W,
+  launch_assemble(nW, S.incW_ptr, S.incW_tet, S.incW_code, WW, S.xyz, S.tets, S.kappa,
+                  o.h1_weighted, valA_W,
                   valH_W, loadW, d_err, st);
 
   // ---- extraction of the blocks used by the solves ----
@@ -821,7 +824,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   // ---- sketch: W = ((H^+)^{-1} L xi)_B ----
   float2* lsplit;
   TRY(M.alloc(&lsplit, (size_t)hp.n_tets * 10, false, st));
-  launch_elem_chol(hp.n_tets, S.xyz, S.tets, lsplit, st);
+  launch_elem_chol(hp.n_tets, S.xyz, S.tets, S.kappa, o.h1_weighted, lsplit, st);
   int32_t *d_ksd, *d_msd, *d_msel;
   TRY(M.upload(&d_ksd, h_k, st));
   TRY(M.upload(&d_msd, h_rank, st));
@@ -1116,7 +1119,7 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, i
   double* res;
   TRY(A.alloc(&lsplit, (size_t)hp.n_tets * 10, false, st));
   TRY(A.alloc(&res, (hp.nP) * (size_t)k, true, st));
-  launch_elem_chol(hp.n_tets, sd->xyz, sd->tets, lsplit, st);
+  launch_elem_chol(hp.n_tets, sd->xyz, sd->tets, sd->kappa, opts->h1_weighted, lsplit, st);
   launch_sketch_rhs(row0, n_rows, sd->p_sd, sd->incP_ptr, sd->incP_tet, sd->incP_code, lsplit,
                     k, opts->seed, res, k, st, nullptr);
   CK(cudaGetLastError());

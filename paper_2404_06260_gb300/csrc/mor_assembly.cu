@@ -8,8 +8,8 @@ __global__ void k_assemble(int64_t n_rows, const int64_t* __restrict__ inc_ptr,
                            const int32_t* __restrict__ inc_tet,
                            const uint32_t* __restrict__ inc_code, int W,
                            const double* __restrict__ xyz, const int32_t* __restrict__ tets,
-                           const double* __restrict__ kappa, double* valA, double* valH,
-                           double* load, int* err) {
+                           const double* __restrict__ kappa, int h1w, double* valA,
+                           double* valH, double* load, int* err) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
   double bl = 0.0;
@@ -23,6 +23,7 @@ __global__ void k_assemble(int64_t n_rows, const int64_t* __restrict__ inc_ptr,
       return;
     }
     double kap = kappa[t];
+    double hk = h1w ? kap : 1.0;  // weight of the gradient part of the H1 form
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       uint32_t slot = (code >> (2 + 7 * b)) & 127u;
@@ -30,7 +31,7 @@ __global__ void k_assemble(int64_t n_rows, const int64_t* __restrict__ inc_ptr,
       double g = dot3(G[a], G[b]) * vol;
       int64_t at = ell_at(r, (int)slot, W);
       valA[at] += kap * g;
-      valH[at] += g + vol * (a == b ? 0.1 : 0.05);
+      valH[at] += hk * g + vol * (a == b ? 0.1 : 0.05);
     }
     bl += 0.25 * vol;
   }
@@ -39,30 +40,35 @@ __global__ void k_assemble(int64_t n_rows, const int64_t* __restrict__ inc_ptr,
 
 void launch_assemble(int64_t n_rows, const int64_t* inc_ptr, const int32_t* inc_tet,
                      const uint32_t* inc_code, int W, const double* xyz, const int32_t* tets,
-                     const double* kappa, double* valA, double* valH, double* load,
-                     int* err, cudaStream_t st) {
+                     const double* kappa, int h1_weighted, double* valA, double* valH,
+                     double* load, int* err, cudaStream_t st) {
   if (n_rows <= 0) return;
   int bs = 128;
   count_launch();
   k_assemble<<<(unsigned)((n_rows + bs - 1) / bs), bs, 0, st>>>(
-      n_rows, inc_ptr, inc_tet, inc_code, W, xyz, tets, kappa, valA, valH, load, err);
+      n_rows, inc_ptr, inc_tet, inc_code, W, xyz, tets, kappa, h1_weighted, valA, valH, load,
+      err);
 }
 
-// element H1 matrix H_T = |T| grad.grad + |T|(1 + d_ab)/20 and its lower Cholesky factor
+// element H1 matrix H_T = w_T |T| grad.grad + |T|(1 + d_ab)/20 (w_T = k_T when the H1
+// form is weighted, else 1) and its lower Cholesky factor
 // L_T (H_T = L_T L_T^T), once per element: the 10 entries L[a][b], b <= a, at
 // a(a+1)/2 + b, each split into binary32 hi + lo (hi = fl32(L), lo = fl32(L - hi)), so
 // the sketch sums can run in double-binary32 arithmetic
 __global__ void k_elem_chol(int64_t n_tets, const double* __restrict__ xyz,
-                            const int32_t* __restrict__ tets, float2* __restrict__ lsplit) {
+                            const int32_t* __restrict__ tets, const double* __restrict__ kappa,
+                            int h1w, float2* __restrict__ lsplit) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n_tets) return;
   double G[4][3], vol;
   tet_gradients(xyz, tets, (int32_t)t, G, vol);
+  const double hk = h1w ? kappa[t] : 1.0;
   double H[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) H[i][j] = dot3(G[i], G[j]) * vol + vol * (i == j ? 0.1 : 0.05);
+    for (int j = 0; j < 4; ++j)
+      H[i][j] = hk * dot3(G[i], G[j]) * vol + vol * (i == j ? 0.1 : 0.05);
   double L[4][4] = {};
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -88,12 +94,13 @@ __global__ void k_elem_chol(int64_t n_tets, const double* __restrict__ xyz,
     }
 }
 
-void launch_elem_chol(int64_t n_tets, const double* xyz, const int32_t* tets, float2* lsplit,
-                      cudaStream_t st) {
+void launch_elem_chol(int64_t n_tets, const double* xyz, const int32_t* tets,
+                      const double* kappa, int h1_weighted, float2* lsplit, cudaStream_t st) {
   if (n_tets <= 0) return;
   int bs = 256;
   count_launch();
-  k_elem_chol<<<(unsigned)((n_tets + bs - 1) / bs), bs, 0, st>>>(n_tets, xyz, tets, lsplit);
+  k_elem_chol<<<(unsigned)((n_tets + bs - 1) / bs), bs, 0, st>>>(n_tets, xyz, tets, kappa,
+                                                                 h1_weighted, lsplit);
 }
 
 // (hi, lo) += x, the rounding error of hi + x kept in lo (Knuth's two-sum)

@@ -21,18 +21,19 @@ int set_error(int code, const std::string& msg);
 // ---------------- assembly (mor_assembly.cu) ----------------
 // Row-gather P1 assembly (Sec. 2, Sec. 4): for every row the element contributions
 // of its incident elements are summed in incidence order (deterministic): stiffness
-// k_T |T| grad(l_a).grad(l_b) into valA, H1 form |T| grad.grad + |T|(1+d_ab)/20
-// into valH, load |T|/4 into load[row].  err is set to 1 on det <= 0.
+// k_T |T| grad(l_a).grad(l_b) into valA, H1 form w_T |T| grad.grad + |T|(1+d_ab)/20
+// into valH (w_T = k_T if h1_weighted, else 1), load |T|/4 into load[row].  err is set
+// to 1 on det <= 0.
 void launch_assemble(int64_t n_rows, const int64_t* inc_ptr, const int32_t* inc_tet,
                      const uint32_t* inc_code, int W, const double* xyz, const int32_t* tets,
-                     const double* kappa, double* valA, double* valH, double* load,
-                     int* err, cudaStream_t st);
+                     const double* kappa, int h1_weighted, double* valA, double* valH,
+                     double* load, int* err, cudaStream_t st);
 
 // Lower Cholesky factor L_T of every element's H1 matrix (the element factors of the
-// field sketch, L L^T = H^+): lsplit[10 t + a(a+1)/2 + b] = L[a][b] (b <= a) as binary32
-// hi + lo.
-void launch_elem_chol(int64_t n_tets, const double* xyz, const int32_t* tets, float2* lsplit,
-                      cudaStream_t st);
+// field sketch, L L^T = H^+; gradient part weighted by k_T if h1_weighted):
+// lsplit[10 t + a(a+1)/2 + b] = L[a][b] (b <= a) as binary32 hi + lo.
+void launch_elem_chol(int64_t n_tets, const double* xyz, const int32_t* tets,
+                      const double* kappa, int h1_weighted, float2* lsplit, cudaStream_t st);
 
 // out[r, j] = sum over incident elements T of (L_T xi_T[:, j])[a(r)], j < k_sd[row_sd[r]]
 // (or j < k when k_sd is null), zero for the other j < k, for rows [row0, row0 + n_rows);

@@ -40,7 +40,7 @@ class BasisOpts(ctypes.Structure):
                 ("max_iter", _i32), ("replace_every", _i32), ("normwise", _i32),
                 ("drift_restart", _dbl),
                 ("sketch_rtol", _dbl), ("tau", _dbl), ("orth_tol", _dbl),
-                ("coarse_rows", _i32)]
+                ("coarse_rows", _i32), ("h1_weighted", _i32)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -11,6 +11,7 @@ from .meshes import (  # noqa: F401
     kuhn_cube,
     lognormal_kappa,
     sphere_kappa,
+    sine_kappa,
     box_owner,
     slab_owner,
     kmeans_owner,

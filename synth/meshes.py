@@ -97,6 +97,14 @@ def lognormal_kappa(n_tets: int, seed: int) -> np.ndarray:
     return np.exp(rng.standard_normal(n_tets))
 
 
+def sine_kappa(mesh: Mesh, k: int) -> np.ndarray:
+    """The oscillating coefficient of the paper's nonconstant-a test (Sec. 7.3),
+    a(x) = 10^k sin(100 x) + 10^k + 1, evaluated at the element centroids (a P0 field);
+    max/min over the cube approaches 2001 for k = 3."""
+    x = mesh.xyz[mesh.tets][:, :, 0].mean(axis=1)
+    return 10.0 ** k * np.sin(100.0 * x) + 10.0 ** k + 1.0
+
+
 def sphere_kappa(mesh: Mesh, seed: int, contrast: float = 1e4, fill: float = 0.10,
                  rmin_h: float = 3.0, rmax_h: float = 6.0) -> np.ndarray:
     """k = 1 background, k = contrast inside seeded random spheres of radius

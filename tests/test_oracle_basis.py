@@ -170,13 +170,16 @@ def test_lemma51_local_bound_in_tolerance_mode(cube16):
             assert num / den < 0.5 * eps
 
 
-def test_field_and_paper_sketch_have_covariance_SB_inverse():
-    # both sketch sources draw W with covariance S_B^{-1} = (R_BB^T R_BB)^{-1}
+@pytest.mark.parametrize("h1_weighted", [False, True])
+def test_field_and_paper_sketch_have_covariance_SB_inverse(h1_weighted):
+    # both sketch sources draw W with covariance S_B^{-1} = (R_BB^T R_BB)^{-1}, for the
+    # H1 form of Sec. 4 and for its coefficient-weighted variant (the element factors
+    # of the field sketch follow the form)
     mesh = synth.kuhn_cube(4)
     kappa = synth.lognormal_kappa(mesh.n_tets, 3)
     owner = synth.slab_owner(4, 2)
     s = subdomains.subdomain_sets(mesh, owner, 0, 1)
-    loc = basis.local_system(mesh, kappa, s)
+    loc = basis.local_system(mesh, kappa, s, h1_weighted=h1_weighted)
     R_BB = basis.weight_rbb(loc["H_plus"], loc["nI"])
     Rinv = sla.solve_triangular(R_BB, np.eye(R_BB.shape[0]))
     cov = Rinv @ Rinv.T
@@ -192,3 +195,21 @@ def test_field_and_paper_sketch_have_covariance_SB_inverse():
         emp = W @ W.T / ncol
         rel = np.linalg.norm(emp - cov) / np.linalg.norm(cov)
         assert rel < 4.0 * sd
+
+
+def test_weighted_h1_form_reduces_to_the_paper_form_for_unit_coefficient():
+    # with k = 1 the coefficient-weighted H1 form is the form of Sec. 4, so the two
+    # variants give the same basis
+    mesh, _, owner, p = synth.workload("cube16_p2")
+    ones = np.ones(mesh.n_tets)
+    s = subdomains.subdomain_sets(mesh, owner, 3, p["r_hops"])
+    a = basis.local_basis(mesh, ones, s, p["rank"], p["oversample"], p["seed"])
+    b = basis.local_basis(mesh, ones, s, p["rank"], p["oversample"], p["seed"],
+                          h1_weighted=True)
+    assert np.array_equal(a["sigma"], b["sigma"])
+    assert np.array_equal(a["Q"], b["Q"])
+    kappa = synth.lognormal_kappa(mesh.n_tets, 3)
+    c = basis.local_basis(mesh, kappa, s, p["rank"], p["oversample"], p["seed"])
+    d = basis.local_basis(mesh, kappa, s, p["rank"], p["oversample"], p["seed"],
+                          h1_weighted=True)
+    assert not np.allclose(c["sigma"], d["sigma"])   # the variant is not a no-op

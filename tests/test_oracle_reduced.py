@@ -56,16 +56,18 @@ def test_galerkin_energy_below_fe_energy_and_monotone_in_rank():
     assert E[0] < E[1] < E[2] <= E_fe * (1 + 1e-13)
 
 
-@pytest.mark.parametrize("explicit", [True, False])
-def test_full_rank_basis_reproduces_fe_solution(explicit):
+@pytest.mark.parametrize("explicit,h1_weighted", [(True, False), (False, False),
+                                                  (False, True)])
+def test_full_rank_basis_reproduces_fe_solution(explicit, h1_weighted):
     # Eq. (9): {u_{i,0}, Z_i phi_1..M} represents the local solution for any trace, so
-    # stitching the full bases reproduces the FE solution (Sec. 5.2 splitting)
+    # stitching the full bases reproduces the FE solution (Sec. 5.2 splitting); the
+    # inner product only weights the SVD, so this holds for the weighted variant too
     n = 12
     mesh = synth.kuhn_cube(n)
     kappa = synth.lognormal_kappa(mesh.n_tets, 7)
     owner = synth.slab_owner(n, 2)
     out = pipeline.run(mesh, kappa, owner, rank=130, oversample=0, r_hops=2, seed=1,
-                       explicit=explicit, keep_all=True, tau=1e-15)
+                       explicit=explicit, keep_all=True, tau=1e-15, h1_weighted=h1_weighted)
     for b, s in zip(out["bases"], out["subs"]):
         assert b["n_kept"] < len(s["owned"])          # a genuine reduction
     assert out["red_err"] < 1e-12
