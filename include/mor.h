@@ -80,6 +80,20 @@ typedef struct {
 int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
                          void* stream, mor_subdomains** out);
 
+/* Step 1 for meshes whose per-subdomain structures do not fit at once (the 440^3
+ * cube of 8000 subdomains: ~6e8 extended rows).  Builds and keeps only the global part
+ * (owned DOFs, interface entries, node -> element incidence) plus host copies of the
+ * mesh connectivity, Dirichlet flags and coordinates.  mor_build_bases then builds the
+ * per-subdomain part in waves of wave_subdomains consecutive subdomains and runs each
+ * wave on the device in turn; mor_project, mor_solve_reduced, mor_lift and
+ * mor_energy_norm work as for mor_build_subdomains.  mor_subdomains_counts reports
+ * only the owned DOFs and r_i (other entries -1); mor_subdomains_indices and
+ * mor_debug_sketch_rhs return MOR_ERR_STATE.  The paper has no counterpart (its
+ * workers each build one subdomain, Sec. 6). */
+int mor_build_subdomains_streamed(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
+                                  int32_t wave_subdomains, void* stream,
+                                  mor_subdomains** out);
+
 /* Sizes of step 1.  counts[host, n_sub x 7] receives per subdomain
  * {|I|, |B|, |omega dofs|, |owned dofs|, |T_i^+|, |omega_i elements|, r_i}; n_sub_out
  * may be NULL.  Pass counts = NULL to query n_sub only. */
@@ -177,7 +191,8 @@ int mor_bases_get_bt(const mor_bases* h, double* out);
 /* Solver statistics of the last mor_build_bases: stats[host, 8] =
  * {iterations of the four local solves (sketch, forward, adjoint, H^+), residual
  * replacements (sum), columns not converged, columns that stopped on the
- * attainable-accuracy test instead of cg_rtol, 0}. */
+ * attainable-accuracy test instead of cg_rtol, 0}; summed over the waves of a
+ * streamed plan. */
 int mor_bases_stats(const mor_bases* h, int64_t* stats);
 
 /* Step 3a (Eq. (23), Sec. 6 step 3): K~ with identity diagonal blocks (from step 2) and

@@ -204,6 +204,14 @@ struct mor_subdomains_s {
   std::vector<int32_t> nbr_ptr, nbr_sd, nbr_blk;
   int64_t n_iface = 0;
   int max_tiles = 0;
+  // streamed plans (mor_build_subdomains_streamed): hp holds the global part only and
+  // mor_build_bases builds the per-subdomain part wave by wave from these host copies
+  bool streamed = false;
+  int wave_sd = 0;
+  int sd_base = 0;  // batch id of this plan's first subdomain (waves of a streamed plan)
+  std::vector<int32_t> h_tets;
+  std::vector<uint8_t> h_dir;
+  std::vector<double> h_xyz;
 };
 
 struct mor_bases_s {
@@ -232,30 +240,14 @@ extern "C" {
 
 const char* mor_last_error(void) { return g_err.c_str(); }
 
-int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
-                         void* stream, mor_subdomains** out) {
-  if (!mesh || !owner || !out) return fail(MOR_ERR_ARG, "mor_build_subdomains: null argument");
-  if (!mesh->xyz_dev || !mesh->tets_dev || !mesh->kappa_dev)
-    return fail(MOR_ERR_ARG, "mor_build_subdomains: null device mesh array");
-  *out = nullptr;
-  cudaStream_t st = (cudaStream_t)stream;
-  auto h = std::make_unique<mor_subdomains_s>();
-  std::string err;
-  // node positions order the rows of each subdomain (Morton order within I and B)
-  std::vector<double> xyz_host;
-  if (mesh->n_nodes > 0) {
-    xyz_host.resize((size_t)mesh->n_nodes * 3);
-    CK(cudaMemcpyAsync(xyz_host.data(), mesh->xyz_dev, xyz_host.size() * sizeof(double),
-                       cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-  }
-  int rc = build_host_plan(mesh->n_nodes, mesh->n_tets, mesh->tets, mesh->dirichlet, owner,
-                           r_hops, xyz_host.empty() ? nullptr : xyz_host.data(), h->hp, err);
-  if (rc != MOR_OK) return fail(rc, err);
+}  // extern "C"
+
+namespace {
+
+// device copies of the per-subdomain part of a plan (sets, row spaces, patterns,
+// incidences, tiles)
+int upload_heavy(mor_subdomains_s* h, cudaStream_t st) {
   const HostPlan& hp = h->hp;
-  h->xyz = mesh->xyz_dev;
-  h->tets = mesh->tets_dev;
-  h->kappa = mesh->kappa_dev;
   Allocs& A = h->mem;
   TRY(A.upload(&h->p_node, hp.p_node, st));
   TRY(A.upload(&h->p_sd, hp.p_sd, st));
@@ -265,8 +257,6 @@ int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_h
   TRY(A.upload(&h->w2p, hp.w2p, st));
   TRY(A.upload(&h->w2o, hp.w2o, st));
   TRY(A.upload(&h->o2w, hp.o2w, st));
-  TRY(A.upload(&h->o_node, hp.o_node, st));
-  TRY(A.upload(&h->o_sd, hp.o_sd, st));
   TRY(A.upload(&h->patP_col, hp.pat_P.col, st));
   TRY(A.upload(&h->patP_w, hp.pat_P.width, st));
   TRY(A.upload(&h->patW_col, hp.pat_W.col, st));
@@ -282,6 +272,17 @@ int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_h
   TRY(upload_tiles(A, hp.tP_B, h->tP_B, st));
   TRY(upload_tiles(A, hp.tW, h->tW, st));
   TRY(upload_tiles(A, hp.tO, h->tO, st));
+  h->max_tiles = std::max({h->tP_all.n, h->tW.n, h->tO.n, h->tP_B.n, 1});
+  return MOR_OK;
+}
+
+// device copies of the global part (O space, interface entries, incidence) and the
+// block-sparse neighbour structure of the reduced matrix
+int upload_light(mor_subdomains_s* h, cudaStream_t st) {
+  const HostPlan& hp = h->hp;
+  Allocs& A = h->mem;
+  TRY(A.upload(&h->o_node, hp.o_node, st));
+  TRY(A.upload(&h->o_sd, hp.o_sd, st));
   TRY(A.upload(&h->pair_ptr, hp.pair_ptr, st));
   TRY(A.upload(&h->e_urow, hp.e_urow, st));
   TRY(A.upload(&h->e_vrow, hp.e_vrow, st));
@@ -290,9 +291,7 @@ int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_h
   TRY(A.upload(&h->n2t_ptr, hp.n2t_ptr, st));
   TRY(A.upload(&h->n2t, hp.n2t, st));
   h->n_iface = (int64_t)hp.e_urow.size();
-  h->max_tiles = std::max({h->tP_all.n, h->tW.n, h->tO.n, h->tP_B.n, 1});
-  // block-sparse neighbour structure of the reduced matrix: pair p gives blocks
-  // 2p = (i, j) and 2p + 1 = (j, i)
+  // pair p gives blocks 2p = (i, j) and 2p + 1 = (j, i)
   std::vector<std::vector<std::pair<int32_t, int32_t>>> rows(hp.n_sd);
   for (size_t p = 0; p < hp.pair_i.size(); ++p) {
     rows[hp.pair_i[p]].emplace_back(hp.pair_j[p], (int32_t)(2 * p));
@@ -307,6 +306,71 @@ int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_h
     }
     h->nbr_ptr.push_back((int32_t)h->nbr_sd.size());
   }
+  return MOR_OK;
+}
+
+int mesh_xyz_host(const mor_mesh* mesh, std::vector<double>& xyz, cudaStream_t st) {
+  xyz.resize((size_t)mesh->n_nodes * 3);
+  if (!xyz.empty()) {
+    CK(cudaMemcpyAsync(xyz.data(), mesh->xyz_dev, xyz.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return MOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
+                         void* stream, mor_subdomains** out) {
+  if (!mesh || !owner || !out) return fail(MOR_ERR_ARG, "mor_build_subdomains: null argument");
+  if (!mesh->xyz_dev || !mesh->tets_dev || !mesh->kappa_dev)
+    return fail(MOR_ERR_ARG, "mor_build_subdomains: null device mesh array");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto h = std::make_unique<mor_subdomains_s>();
+  std::string err;
+  // node positions order the rows of each subdomain (Morton order within I and B)
+  std::vector<double> xyz_host;
+  TRY(mesh_xyz_host(mesh, xyz_host, st));
+  int rc = build_host_plan(mesh->n_nodes, mesh->n_tets, mesh->tets, mesh->dirichlet, owner,
+                           r_hops, xyz_host.empty() ? nullptr : xyz_host.data(), h->hp, err);
+  if (rc != MOR_OK) return fail(rc, err);
+  h->xyz = mesh->xyz_dev;
+  h->tets = mesh->tets_dev;
+  h->kappa = mesh->kappa_dev;
+  TRY(upload_heavy(h.get(), st));
+  TRY(upload_light(h.get(), st));
+  CK(cudaStreamSynchronize(st));
+  *out = h.release();
+  return MOR_OK;
+}
+
+int mor_build_subdomains_streamed(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
+                                  int32_t wave_subdomains, void* stream,
+                                  mor_subdomains** out) {
+  if (!mesh || !owner || !out || wave_subdomains < 1)
+    return fail(MOR_ERR_ARG, "mor_build_subdomains_streamed: bad argument");
+  if (!mesh->xyz_dev || !mesh->tets_dev || !mesh->kappa_dev)
+    return fail(MOR_ERR_ARG, "mor_build_subdomains_streamed: null device mesh array");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto h = std::make_unique<mor_subdomains_s>();
+  std::string err;
+  int rc = build_global_plan(mesh->n_nodes, mesh->n_tets, mesh->tets, mesh->dirichlet, owner,
+                             r_hops, h->hp, err);
+  if (rc != MOR_OK) return fail(rc, err);
+  h->streamed = true;
+  h->wave_sd = wave_subdomains;
+  h->h_tets.assign(mesh->tets, mesh->tets + 4 * mesh->n_tets);
+  h->h_dir.assign(mesh->dirichlet, mesh->dirichlet + mesh->n_nodes);
+  TRY(mesh_xyz_host(mesh, h->h_xyz, st));
+  h->xyz = mesh->xyz_dev;
+  h->tets = mesh->tets_dev;
+  h->kappa = mesh->kappa_dev;
+  TRY(upload_light(h.get(), st));
   CK(cudaStreamSynchronize(st));
   *out = h.release();
   return MOR_OK;
@@ -315,6 +379,16 @@ int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_h
 int mor_subdomains_counts(const mor_subdomains* h, int32_t* n_sub_out, int64_t* counts) {
   if (!h) return fail(MOR_ERR_ARG, "mor_subdomains_counts: null handle");
   if (n_sub_out) *n_sub_out = h->hp.n_sd;
+  if (counts && h->streamed) {
+    // only the global part is kept: owned DOFs and hops; the rest is -1
+    for (int i = 0; i < h->hp.n_sd; ++i) {
+      int64_t* c = counts + 7 * (int64_t)i;
+      for (int q = 0; q < 7; ++q) c[q] = -1;
+      c[3] = h->hp.Ooff[i + 1] - h->hp.Ooff[i];
+      c[6] = (int64_t)h->hp.r_sd[i];
+    }
+    return MOR_OK;
+  }
   if (counts)
     for (int i = 0; i < h->hp.n_sd; ++i) {
       const SubSets& s = h->hp.sets[i];
@@ -333,6 +407,8 @@ int mor_subdomains_counts(const mor_subdomains* h, int32_t* n_sub_out, int64_t* 
 int mor_subdomains_indices(const mor_subdomains* h, int32_t sub, int32_t which, int32_t* out) {
   if (!h || !out || sub < 0 || sub >= h->hp.n_sd || which < 0 || which > 5)
     return fail(MOR_ERR_ARG, "mor_subdomains_indices: bad argument");
+  if (h->streamed)
+    return fail(MOR_ERR_STATE, "mor_subdomains_indices: streamed plans keep no index sets");
   const SubSets& s = h->hp.sets[sub];
   const std::vector<int32_t>* v[6] = {&s.I, &s.B, &s.omega, &s.owned, &s.plus_tets,
                                       &s.omega_tets};
@@ -534,8 +610,10 @@ struct Build {
 
 }  // namespace
 
-extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* opts,
-                               void* stream, mor_bases** out) {
+// step 2 for every subdomain of a plan whose per-subdomain part is on the device;
+// m_force > 0 fixes the widest rank (so that waves of a streamed plan share k and kq)
+static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts,
+                            int m_force, void* stream, mor_bases** out) {
   if (!sd || !opts || !out) return fail(MOR_ERR_ARG, "mor_build_bases: null argument");
   *out = nullptr;
   const mor_basis_opts& o = *opts;
@@ -549,6 +627,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
     h_k[i] = h_rank[i] + o.oversample;
     m_max = std::max(m_max, h_rank[i]);
   }
+  if (m_force > 0) m_max = std::max(m_max, m_force);
   const int k = m_max + o.oversample;     // widest sketch; the load column sits at k
   const int kp = round_up4(k + 1);
   const bool tol_mode = o.eps > 0.0;
@@ -830,7 +909,7 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   TRY(M.upload(&d_msd, h_rank, st));
   TRY(M.alloc(&d_msel, n_sd, true, st));
   launch_sketch_rhs(0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lsplit, k, o.seed,
-                    vS, kp, st, d_ksd);
+                    (uint32_t)S.sd_base, vS, kp, st, d_ksd);
   TRY(solve(S.tP_all, Hp, false, vS, vG, k, 0, rt_sketch));
 
   // ---- forward solve A_II [X | u_0] = [A_IB W | b_I] (Prob. "aux1", Eq. (7), and the lifting of Eq. (8)) ----
@@ -925,7 +1004,83 @@ extern "C" int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* o
   return MOR_OK;
 }
 
+// streamed plans: the per-subdomain part of waves of sd->wave_sd subdomains is built on
+// the host, uploaded, and run through build_bases_core; Q, b~, sigma and the kept
+// counts of each wave go to their rows of the global handle
+static int build_bases_streamed(const mor_subdomains* sd, const mor_basis_opts* opts,
+                                void* stream, mor_bases** out) {
+  const HostPlan& g = sd->hp;
+  const mor_basis_opts& o = *opts;
+  cudaStream_t st = (cudaStream_t)stream;
+  int m_max = 0;
+  for (int i = 0; i < g.n_sd; ++i) m_max = std::max(m_max, o.ranks ? o.ranks[i] : o.rank);
+  auto bases = std::make_unique<mor_bases_s>();
+  mor_bases_s& Bo = *bases;
+  PlanScratch ps;
+  int64_t not_conv = 0;
+  for (int s0 = 0; s0 < g.n_sd; s0 += sd->wave_sd) {
+    const int s1 = std::min(g.n_sd, s0 + sd->wave_sd), nw = s1 - s0;
+    auto W = std::make_unique<mor_subdomains_s>();
+    std::string err;
+    int rc = build_wave_plan(g.n_nodes, g.n_tets, sd->h_tets.data(), sd->h_dir.data(),
+                             sd->h_xyz.data(), g, s0, s1, W->hp, ps, err);
+    if (rc != MOR_OK) return fail(rc, err);
+    W->xyz = sd->xyz;
+    W->tets = sd->tets;
+    W->kappa = sd->kappa;
+    W->sd_base = s0;
+    TRY(upload_heavy(W.get(), st));
+    mor_basis_opts ow = o;
+    if (o.ranks) ow.ranks = o.ranks + s0;
+    mor_bases* bw = nullptr;
+    rc = build_bases_core(W.get(), &ow, m_max, stream, &bw);
+    std::unique_ptr<mor_bases_s> wb(bw);
+    if (rc == MOR_ERR_NOT_CONVERGED)
+      not_conv += wb->stats[5];
+    else if (rc != MOR_OK)
+      return rc;
+    if (s0 == 0) {
+      Bo.n_sd = g.n_sd;
+      Bo.k = wb->k;
+      Bo.kp = wb->kp;
+      Bo.kq = wb->kq;
+      Bo.m = wb->m;
+      Bo.Ooff = g.Ooff;
+      TRY(Bo.mem.alloc(&Bo.Q, (size_t)g.nO * Bo.kq, true, st));
+      TRY(Bo.mem.alloc(&Bo.bt, (size_t)g.n_sd * Bo.kq, true, st));
+      TRY(Bo.mem.alloc(&Bo.sigma, (size_t)g.n_sd * Bo.kp, true, st));
+      TRY(Bo.mem.alloc(&Bo.kept, g.n_sd, true, st));
+      Bo.h_kept.assign(g.n_sd, 0);
+      Bo.h_sigma.assign((size_t)g.n_sd * Bo.kp, 0.0);
+    }
+    const int64_t o0 = g.Ooff[s0], no = g.Ooff[s1] - o0;
+    CK(cudaMemcpyAsync(Bo.Q + o0 * Bo.kq, wb->Q, (size_t)no * Bo.kq * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(Bo.bt + (int64_t)s0 * Bo.kq, wb->bt, (size_t)nw * Bo.kq * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(Bo.sigma + (int64_t)s0 * Bo.kp, wb->sigma,
+                       (size_t)nw * Bo.kp * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(Bo.kept + s0, wb->kept, nw * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    std::copy(wb->h_kept.begin(), wb->h_kept.end(), Bo.h_kept.begin() + s0);
+    std::copy(wb->h_sigma.begin(), wb->h_sigma.end(), Bo.h_sigma.begin() + (int64_t)s0 * Bo.kp);
+    for (int q = 0; q < 8; ++q) Bo.stats[q] += wb->stats[q];
+    CK(cudaStreamSynchronize(st));  // the wave's memory is released after its copies
+  }
+  *out = bases.release();
+  if (not_conv > 0)
+    return fail(MOR_ERR_NOT_CONVERGED, "mor_build_bases: " + std::to_string(not_conv) +
+                                           " local solve columns did not converge");
+  return MOR_OK;
+}
+
 extern "C" {
+
+int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* opts, void* stream,
+                    mor_bases** out) {
+  if (!sd || !opts || !out) return fail(MOR_ERR_ARG, "mor_build_bases: null argument");
+  if (sd->streamed) return build_bases_streamed(sd, opts, stream, out);
+  return build_bases_core(sd, opts, 0, stream, out);
+}
 
 int mor_bases_info(const mor_bases* h, int32_t* kq, int32_t* k, int32_t* kept,
                    int64_t* total_kept) {
@@ -1110,6 +1265,8 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, i
                          double* out, void* stream) {
   if (!sd || !opts || !out || sub < 0 || sub >= sd->hp.n_sd)
     return fail(MOR_ERR_ARG, "mor_debug_sketch_rhs: bad argument");
+  if (sd->streamed)
+    return fail(MOR_ERR_STATE, "mor_debug_sketch_rhs: not available for streamed plans");
   const HostPlan& hp = sd->hp;
   cudaStream_t st = (cudaStream_t)stream;
   int k = opts->rank + opts->oversample;
@@ -1121,7 +1278,7 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, i
   TRY(A.alloc(&res, (hp.nP) * (size_t)k, true, st));
   launch_elem_chol(hp.n_tets, sd->xyz, sd->tets, sd->kappa, opts->h1_weighted, lsplit, st);
   launch_sketch_rhs(row0, n_rows, sd->p_sd, sd->incP_ptr, sd->incP_tet, sd->incP_code, lsplit,
-                    k, opts->seed, res, k, st, nullptr);
+                    k, opts->seed, 0u, res, k, st, nullptr);
   CK(cudaGetLastError());
   std::vector<double> tmp((size_t)n_rows * k);
   CK(cudaMemcpyAsync(tmp.data(), res + row0 * k, tmp.size() * sizeof(double),

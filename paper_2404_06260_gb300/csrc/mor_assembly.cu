@@ -120,13 +120,14 @@ __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __rest
                              const int32_t* __restrict__ inc_tet,
                              const uint32_t* __restrict__ inc_code,
                              const float2* __restrict__ lsplit, int k, uint64_t seed,
-                             double* __restrict__ out, int ld,
+                             uint32_t sd_base, double* __restrict__ out, int ld,
                              const int32_t* __restrict__ k_sd) {
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= n_rows) return;
   int64_t r = row0 + w;
   uint32_t sd = (uint32_t)row_sd[r];
+  const uint32_t sd_id = sd + sd_base;  // the subdomain's id in the whole batch
   int64_t q0 = inc_ptr[r], q1 = inc_ptr[r + 1];
   const int kk = k_sd ? min(k, (int)k_sd[sd]) : k;
   for (int j = lane + kk; j < k; j += 32) out[r * ld + j] = 0.0;
@@ -135,7 +136,7 @@ __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __rest
     for (int64_t q = q0; q < q1; ++q) {
       float z[4];
       const uint32_t t = (uint32_t)inc_tet[q];
-      field_normals(t, (uint32_t)j, sd, seed, z);
+      field_normals(t, (uint32_t)j, sd_id, seed, z);
       const int a = inc_code[q] & 3u;
       const float2* La = lsplit + 10 * (int64_t)t + a * (a + 1) / 2;
       for (int b = 0; b <= a; ++b) {
@@ -153,13 +154,14 @@ __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __rest
 void launch_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int64_t* inc_ptr, const int32_t* inc_tet,
                        const uint32_t* inc_code, const float2* lsplit, int k, uint64_t seed,
-                       double* out, int ld, cudaStream_t st, const int32_t* k_sd) {
+                       uint32_t sd_base, double* out, int ld, cudaStream_t st,
+                       const int32_t* k_sd) {
   if (n_rows <= 0) return;
   int bs = 256;
   unsigned grid = (unsigned)((n_rows * 32 + bs - 1) / bs);
   count_launch();
   k_sketch_rhs<<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, inc_code, lsplit,
-                                    k, seed, out, ld, k_sd);
+                                    k, seed, sd_base, out, ld, k_sd);
 }
 
 // one thread per destination row; warps cover whole slices so the slice width is a

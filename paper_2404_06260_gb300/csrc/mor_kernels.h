@@ -37,11 +37,13 @@ void launch_elem_chol(int64_t n_tets, const double* xyz, const int32_t* tets,
 
 // out[r, j] = sum over incident elements T of (L_T xi_T[:, j])[a(r)], j < k_sd[row_sd[r]]
 // (or j < k when k_sd is null), zero for the other j < k, for rows [row0, row0 + n_rows);
-// xi from Philox counter (T, j, row_sd[r], 0); products and sums in double-binary32.
+// xi from Philox counter (T, j, sd_base + row_sd[r], 0) (sd_base: the batch id of the
+// plan's first subdomain); products and sums in double-binary32.
 void launch_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int64_t* inc_ptr, const int32_t* inc_tet,
                        const uint32_t* inc_code, const float2* lsplit, int k, uint64_t seed,
-                       double* out, int ld, cudaStream_t st, const int32_t* k_sd);
+                       uint32_t sd_base, double* out, int ld, cudaStream_t st,
+                       const int32_t* k_sd);
 
 // Extract a sliced-ELL matrix from an assembled pattern: destination row r takes source
 // row s = row_src ? row_src[r] : r when row_cls is null or row_cls[s] == row_want;

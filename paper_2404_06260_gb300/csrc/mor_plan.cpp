@@ -205,9 +205,9 @@ void morton_order(const double* xyz, const std::vector<int32_t>& I,
 
 }  // namespace
 
-int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
-                    const uint8_t* dirichlet, const int32_t* owner, int32_t r_hops,
-                    const double* xyz, HostPlan& hp, std::string& err) {
+int build_global_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
+                      const uint8_t* dirichlet, const int32_t* owner, int32_t r_hops,
+                      HostPlan& g, std::string& err) {
   if (n_nodes <= 0 || n_tets <= 0 || !tets || !dirichlet || !owner) {
     err = "mor_build_subdomains: empty mesh or null array";
     return MOR_ERR_ARG;
@@ -233,56 +233,143 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     }
     n_sd = std::max(n_sd, owner[v] + 1);
   }
-  hp = HostPlan();
-  hp.n_nodes = n_nodes;
-  hp.n_tets = n_tets;
-  hp.n_sd = n_sd;
-  hp.r_hops = r_hops;
+  g = HostPlan();
+  g.n_nodes = n_nodes;
+  g.n_tets = n_tets;
+  g.n_sd = n_sd;
+  g.r_hops = r_hops;
 
   // global node -> element incidence (ascending element ids)
-  hp.n2t_ptr.assign(n_nodes + 1, 0);
-  for (int64_t q = 0; q < 4 * n_tets; ++q) hp.n2t_ptr[tets[q] + 1]++;
-  for (int64_t v = 0; v < n_nodes; ++v) hp.n2t_ptr[v + 1] += hp.n2t_ptr[v];
-  hp.n2t.assign(4 * n_tets, 0);
+  g.n2t_ptr.assign(n_nodes + 1, 0);
+  for (int64_t q = 0; q < 4 * n_tets; ++q) g.n2t_ptr[tets[q] + 1]++;
+  for (int64_t v = 0; v < n_nodes; ++v) g.n2t_ptr[v + 1] += g.n2t_ptr[v];
+  g.n2t.assign(4 * n_tets, 0);
   {
-    std::vector<int64_t> fill(hp.n2t_ptr.begin(), hp.n2t_ptr.end() - 1);
+    std::vector<int64_t> fill(g.n2t_ptr.begin(), g.n2t_ptr.end() - 1);
     for (int64_t e = 0; e < n_tets; ++e)
-      for (int a = 0; a < 4; ++a) hp.n2t[fill[tets[4 * e + a]]++] = (int32_t)e;
+      for (int a = 0; a < 4; ++a) g.n2t[fill[tets[4 * e + a]]++] = (int32_t)e;
   }
 
   // owned nodes per subdomain (ascending)
-  std::vector<std::vector<int32_t>> P(n_sd);
-  for (int64_t v = 0; v < n_nodes; ++v) P[owner[v]].push_back((int32_t)v);
+  g.Pown.assign(n_sd, {});
+  for (int64_t v = 0; v < n_nodes; ++v) g.Pown[owner[v]].push_back((int32_t)v);
   for (int i = 0; i < n_sd; ++i)
-    if (P[i].empty()) {
+    if (g.Pown[i].empty()) {
       err = "mor_build_subdomains: owner label " + std::to_string(i) + " is unused";
       return MOR_ERR_ARG;
     }
-
-  int n_threads = (int)std::max(1u, std::thread::hardware_concurrency());
-  n_threads = std::min(n_threads, 32);
   // hops per subdomain: fixed, or about half the width of the owned set
   // (max(1, round(cbrt(|P_i|) / 2)): the extension roughly doubles the diameter)
-  hp.r_sd.resize(n_sd);
+  g.r_sd.resize(n_sd);
   for (int i = 0; i < n_sd; ++i)
-    hp.r_sd[i] = r_hops > 0 ? r_hops
-                            : std::max(1, (int32_t)std::lround(std::cbrt((double)P[i].size()) / 2.0));
-  std::vector<Scratch> scratch(std::min(n_threads, n_sd));
-  for (auto& s : scratch) s.init(n_nodes, n_tets);
-  hp.sets.resize(n_sd);
-  std::vector<SubOut> outs(n_sd);
-  const auto& n2t_ptr = hp.n2t_ptr;
-  const auto& n2t = hp.n2t;
+    g.r_sd[i] = r_hops > 0 ? r_hops
+                           : std::max(1, (int32_t)std::lround(std::cbrt((double)g.Pown[i].size()) / 2.0));
 
-  parallel_for(n_sd, (int)scratch.size(), [&](int i, int t) {
+  // owned free nodes (O space, by subdomain, ascending node ids)
+  g.Ooff.assign(n_sd + 1, 0);
+  for (int i = 0; i < n_sd; ++i) {
+    int64_t c = 0;
+    for (int32_t v : g.Pown[i]) c += dirichlet[v] == 0;
+    g.Ooff[i + 1] = g.Ooff[i] + c;
+  }
+  g.nO = g.Ooff[n_sd];
+  g.o_node.resize(g.nO);
+  g.o_sd.resize(g.nO);
+  std::vector<int32_t> g_node2orow(n_nodes, -1);
+  for (int i = 0; i < n_sd; ++i) {
+    int64_t o = g.Ooff[i];
+    for (int32_t v : g.Pown[i])
+      if (!dirichlet[v]) {
+        g.o_node[o] = v;
+        g.o_sd[o] = i;
+        g_node2orow[v] = (int32_t)o;
+        ++o;
+      }
+  }
+
+  // interface entries: free u, v sharing an element, owner(u) < owner(v)
+  struct Entry {
+    int32_t i, j, u, v;
+    bool operator<(const Entry& o) const {
+      if (i != o.i) return i < o.i;
+      if (j != o.j) return j < o.j;
+      if (u != o.u) return u < o.u;
+      return v < o.v;
+    }
+    bool operator==(const Entry& o) const {
+      return i == o.i && j == o.j && u == o.u && v == o.v;
+    }
+  };
+  std::vector<Entry> ents;
+  for (int64_t u = 0; u < n_nodes; ++u) {
+    if (dirichlet[u]) continue;
+    for (int64_t q = g.n2t_ptr[u]; q < g.n2t_ptr[u + 1]; ++q)
+      for (int b = 0; b < 4; ++b) {
+        int32_t v = tets[4 * (int64_t)g.n2t[q] + b];
+        if (dirichlet[v] || owner[v] <= owner[u]) continue;
+        ents.push_back(Entry{owner[u], owner[v], (int32_t)u, v});
+      }
+  }
+  std::sort(ents.begin(), ents.end());
+  ents.erase(std::unique(ents.begin(), ents.end()), ents.end());
+  g.pair_ptr.assign(1, 0);
+  for (size_t q = 0; q < ents.size(); ++q) {
+    if (q == 0 || ents[q].i != ents[q - 1].i || ents[q].j != ents[q - 1].j) {
+      if (q > 0) g.pair_ptr.push_back((int64_t)q);
+      g.pair_i.push_back(ents[q].i);
+      g.pair_j.push_back(ents[q].j);
+    }
+    g.e_urow.push_back(g_node2orow[ents[q].u]);
+    g.e_vrow.push_back(g_node2orow[ents[q].v]);
+    g.e_unode.push_back(ents[q].u);
+    g.e_vnode.push_back(ents[q].v);
+  }
+  if (!ents.empty()) g.pair_ptr.push_back((int64_t)ents.size());
+  return MOR_OK;
+}
+
+// per-thread work arrays of the wave builder, stamped with subdomain id + 1
+struct PlanScratch::Impl {
+  std::vector<Scratch> s;
+};
+PlanScratch::PlanScratch() : impl(new Impl) {}
+PlanScratch::~PlanScratch() { delete impl; }
+
+int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
+                    const uint8_t* dirichlet, const double* xyz, const HostPlan& g, int s0,
+                    int s1, HostPlan& w, PlanScratch& ps, std::string& err) {
+  const int nw = s1 - s0;
+  w = HostPlan();
+  w.n_nodes = n_nodes;
+  w.n_tets = n_tets;
+  w.n_sd = nw;
+  w.r_hops = g.r_hops;
+  w.r_sd.assign(g.r_sd.begin() + s0, g.r_sd.begin() + s1);
+  // per-thread scratch: 6 node arrays + 2 element flag arrays; at most 32 threads and
+  // about 24 GB of scratch in total
+  const double per_thread = 24.0 * (double)n_nodes + 2.0 * (double)n_tets;
+  int nthr = (int)std::max(1u, std::thread::hardware_concurrency());
+  nthr = std::min({nthr, 32, std::max(1, (int)(24e9 / per_thread)), std::max(nw, 1)});
+  auto& scratch = ps.impl->s;
+  while ((int)scratch.size() < nthr) {
+    scratch.emplace_back();
+    scratch.back().init(n_nodes, n_tets);
+  }
+  w.sets.resize(nw);
+  std::vector<SubOut> outs(nw);
+  const auto& n2t_ptr = g.n2t_ptr;
+  const auto& n2t = g.n2t;
+
+  parallel_for(nw, nthr, [&](int li, int t) {
     Scratch& S = scratch[t];
+    const int i = s0 + li;
     const int32_t st = i + 1;
-    SubSets& ss = hp.sets[i];
-    SubOut& so = outs[i];
+    SubSets& ss = w.sets[li];
+    SubOut& so = outs[li];
     // r-hop ball of P_i over element edges
-    std::vector<int32_t> ball_list = P[i], frontier = P[i], next;
-    for (int32_t v : P[i]) S.ball[v] = st;
-    for (int h = 0; h < hp.r_sd[i]; ++h) {
+    std::vector<int32_t> ball_list = g.Pown[i], frontier = g.Pown[i], next;
+    for (int32_t v : g.Pown[i]) S.ball[v] = st;
+    for (int h = 0; h < g.r_sd[i]; ++h) {
       next.clear();
       for (int32_t v : frontier)
         for (int64_t q = n2t_ptr[v]; q < n2t_ptr[v + 1]; ++q)
@@ -321,7 +408,7 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     std::sort(ss.I.begin(), ss.I.end());
     std::sort(ss.B.begin(), ss.B.end());
     // omega_i = elements touching P_i
-    for (int32_t v : P[i])
+    for (int32_t v : g.Pown[i])
       for (int64_t q = n2t_ptr[v]; q < n2t_ptr[v + 1]; ++q) {
         int32_t e = n2t[q];
         if (!S.tomega[e]) {
@@ -339,7 +426,7 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
       }
     std::sort(ss.omega.begin(), ss.omega.end());
     for (size_t w = 0; w < ss.omega.size(); ++w) S.wloc[ss.omega[w]] = (int32_t)w;
-    for (int32_t v : P[i])
+    for (int32_t v : g.Pown[i])
       if (!dirichlet[v]) ss.owned.push_back(v);
     // plus-local numbering: I then B, each in Morton order
     morton_order(xyz, ss.I, ss.B, ss.Ip, ss.Bp, ss.pcode);
@@ -377,7 +464,8 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
       err = "mor_build_subdomains: " + o.err;
       return MOR_ERR_ARG;
     }
-
+  HostPlan& hp = w;
+  const int n_sd = nw;
   // batched layouts
   hp.Poff.assign(n_sd + 1, 0);
   hp.Woff.assign(n_sd + 1, 0);
@@ -410,7 +498,6 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
   hp.o2w.resize(hp.nO);
   hp.o_node.resize(hp.nO);
   hp.o_sd.resize(hp.nO);
-  std::vector<int32_t> node2orow(n_nodes, -1);
   for (int i = 0; i < n_sd; ++i) {
     const SubSets& ss = hp.sets[i];
     int64_t p0 = hp.Poff[i], w0 = hp.Woff[i], o0 = hp.Ooff[i];
@@ -436,7 +523,6 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
       hp.w2o[wr] = (int32_t)(o0 + o);
       hp.o_node[o0 + o] = ss.owned[o];
       hp.o_sd[o0 + o] = i;
-      node2orow[ss.owned[o]] = (int32_t)(o0 + o);
     }
   }
   pack_ell(outs, true, hp.Poff, hp.nP, hp.pat_P, hp.incP_ptr, hp.incP_tet, hp.incP_code);
@@ -473,44 +559,29 @@ int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     make_tiles(b, e, hp.tO);
   }
 
-  // interface entries: free u, v sharing an element, owner(u) < owner(v)
-  struct Entry {
-    int32_t i, j, u, v;
-    bool operator<(const Entry& o) const {
-      if (i != o.i) return i < o.i;
-      if (j != o.j) return j < o.j;
-      if (u != o.u) return u < o.u;
-      return v < o.v;
-    }
-    bool operator==(const Entry& o) const {
-      return i == o.i && j == o.j && u == o.u && v == o.v;
-    }
-  };
-  std::vector<Entry> ents;
-  for (int64_t u = 0; u < n_nodes; ++u) {
-    if (dirichlet[u]) continue;
-    for (int64_t q = hp.n2t_ptr[u]; q < hp.n2t_ptr[u + 1]; ++q)
-      for (int b = 0; b < 4; ++b) {
-        int32_t v = tets[4 * (int64_t)hp.n2t[q] + b];
-        if (dirichlet[v] || owner[v] <= owner[u]) continue;
-        ents.push_back(Entry{owner[u], owner[v], (int32_t)u, v});
-      }
-  }
-  std::sort(ents.begin(), ents.end());
-  ents.erase(std::unique(ents.begin(), ents.end()), ents.end());
-  hp.pair_ptr.assign(1, 0);
-  for (size_t q = 0; q < ents.size(); ++q) {
-    if (q == 0 || ents[q].i != ents[q - 1].i || ents[q].j != ents[q - 1].j) {
-      if (q > 0) hp.pair_ptr.push_back((int64_t)q);
-      hp.pair_i.push_back(ents[q].i);
-      hp.pair_j.push_back(ents[q].j);
-    }
-    hp.e_urow.push_back(node2orow[ents[q].u]);
-    hp.e_vrow.push_back(node2orow[ents[q].v]);
-    hp.e_unode.push_back(ents[q].u);
-    hp.e_vnode.push_back(ents[q].v);
-  }
-  if (!ents.empty()) hp.pair_ptr.push_back((int64_t)ents.size());
+  return MOR_OK;
+}
+
+int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
+                    const uint8_t* dirichlet, const int32_t* owner, int32_t r_hops,
+                    const double* xyz, HostPlan& hp, std::string& err) {
+  HostPlan g;
+  int rc = build_global_plan(n_nodes, n_tets, tets, dirichlet, owner, r_hops, g, err);
+  if (rc != MOR_OK) return rc;
+  PlanScratch ps;
+  rc = build_wave_plan(n_nodes, n_tets, tets, dirichlet, xyz, g, 0, g.n_sd, hp, ps, err);
+  if (rc != MOR_OK) return rc;
+  // the global parts: incidence, owned sets, interface entries
+  hp.n2t_ptr.swap(g.n2t_ptr);
+  hp.n2t.swap(g.n2t);
+  hp.Pown.swap(g.Pown);
+  hp.pair_i.swap(g.pair_i);
+  hp.pair_j.swap(g.pair_j);
+  hp.pair_ptr.swap(g.pair_ptr);
+  hp.e_urow.swap(g.e_urow);
+  hp.e_vrow.swap(g.e_vrow);
+  hp.e_unode.swap(g.e_unode);
+  hp.e_vnode.swap(g.e_vnode);
   return MOR_OK;
 }
 

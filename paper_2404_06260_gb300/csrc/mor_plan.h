@@ -50,6 +50,7 @@ struct HostPlan {
   std::vector<int32_t> p_node, p_sd, w_node, w_sd, w2p, w2o, o2w, o_node, o_sd;
   std::vector<uint8_t> p_isB;
   std::vector<uint32_t> p_code;  // 30-bit Morton code of each P row (see SubSets)
+  std::vector<std::vector<int32_t>> Pown;  // owned nodes of each subdomain (global plan)
   // patterns on T_i^+ (P space) and omega_i (W space); columns are space indices
   HostEll pat_P, pat_W;
   // assembly incidence, CSR over rows: element id and code
@@ -91,5 +92,26 @@ void build_aggregates(const HostPlan& hp, int target_rows, int max_agg, AggPlan&
 int build_host_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
                     const uint8_t* dirichlet, const int32_t* owner, int32_t r_hops,
                     const double* xyz, HostPlan& hp, std::string& err);
+
+// The two halves of build_host_plan, for meshes whose per-subdomain structures do not fit
+// at once.  build_global_plan: n_sd, r_sd, node -> element incidence, owned sets (Pown),
+// the global O space (Ooff, o_node, o_sd) and the interface entries.  build_wave_plan:
+// the per-subdomain sets, row spaces, patterns, incidences and tiles of subdomains
+// [s0, s1), numbered 0 .. s1 - s0 - 1, using the incidence and owned sets of g; its O
+// rows are the global O rows [g.Ooff[s0], g.Ooff[s1]) in the same order.
+struct PlanScratch {
+  struct Impl;
+  Impl* impl;
+  PlanScratch();
+  ~PlanScratch();
+  PlanScratch(const PlanScratch&) = delete;
+  PlanScratch& operator=(const PlanScratch&) = delete;
+};
+int build_global_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
+                      const uint8_t* dirichlet, const int32_t* owner, int32_t r_hops,
+                      HostPlan& g, std::string& err);
+int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
+                    const uint8_t* dirichlet, const double* xyz, const HostPlan& g, int s0,
+                    int s1, HostPlan& w, PlanScratch& ps, std::string& err);
 
 }  // namespace mor

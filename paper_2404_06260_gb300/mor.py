@@ -56,6 +56,8 @@ def _sig(name, res, *args):
 
 
 _sig("mor_build_subdomains", _i32, ctypes.POINTER(_MeshC), _P, _i32, _P, ctypes.POINTER(_P))
+_sig("mor_build_subdomains_streamed", _i32, ctypes.POINTER(_MeshC), _P, _i32, _i32, _P,
+     ctypes.POINTER(_P))
 _sig("mor_subdomains_counts", _i32, _P, ctypes.POINTER(_i32), _P)
 _sig("mor_subdomains_indices", _i32, _P, _i32, _i32, _P)
 _sig("mor_basis_opts_default", _i32, ctypes.POINTER(BasisOpts))
@@ -84,7 +86,8 @@ _sig("mor_free_bases", None, _P)
 _sig("mor_free_reduced", None, _P)
 _sig("mor_last_error", ctypes.c_char_p)
 
-EXPORTED = ["mor_build_subdomains", "mor_subdomains_counts", "mor_subdomains_indices",
+EXPORTED = ["mor_build_subdomains", "mor_build_subdomains_streamed", "mor_subdomains_counts",
+            "mor_subdomains_indices",
             "mor_basis_opts_default", "mor_build_bases", "mor_bases_info", "mor_bases_sigma",
             "mor_bases_get_Q", "mor_bases_get_bt", "mor_bases_stats", "mor_project",
             "mor_reduced_info", "mor_reduced_dense", "mor_solve_reduced",
@@ -147,13 +150,22 @@ class Mesh:
 
 
 class Subdomains:
-    def __init__(self, mesh: Mesh, owner, r_hops: int, stream=None):
+    """Step 1.  wave > 0 builds a streamed plan (mor_build_subdomains_streamed):
+    mor_build_bases then works in waves of `wave` subdomains."""
+
+    def __init__(self, mesh: Mesh, owner, r_hops: int, stream=None, wave: int = 0):
         self.mesh = mesh
         self._owner = np.ascontiguousarray(owner, dtype=np.int32)
+        self.streamed = wave > 0
         h = _P()
         mc = mesh._c()
-        _check(_lib.mor_build_subdomains(ctypes.byref(mc), _ptr(self._owner), int(r_hops),
-                                         _stream(stream), ctypes.byref(h)))
+        if self.streamed:
+            _check(_lib.mor_build_subdomains_streamed(ctypes.byref(mc), _ptr(self._owner),
+                                                      int(r_hops), int(wave),
+                                                      _stream(stream), ctypes.byref(h)))
+        else:
+            _check(_lib.mor_build_subdomains(ctypes.byref(mc), _ptr(self._owner),
+                                             int(r_hops), _stream(stream), ctypes.byref(h)))
         self.h = h
         n = _i32()
         _check(_lib.mor_subdomains_counts(h, ctypes.byref(n), None))
@@ -162,9 +174,11 @@ class Subdomains:
         _check(_lib.mor_subdomains_counts(h, None, _ptr(self.counts)))
 
     def indices(self, sub: int, which: int) -> np.ndarray:
-        out = np.zeros(int(self.counts[sub, which]), dtype=np.int32)
+        # streamed plans keep no index sets (count -1): the library answers MOR_ERR_STATE
+        n = int(self.counts[sub, which])
+        out = np.zeros(max(n, 1), dtype=np.int32)
         _check(_lib.mor_subdomains_indices(self.h, int(sub), int(which), _ptr(out)))
-        return out
+        return out[:max(n, 0)]
 
     def __del__(self):
         if getattr(self, "h", None):
