@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <future>
 #include <mutex>
 #include <array>
 #include <atomic>
@@ -1018,13 +1019,25 @@ static int build_bases_streamed(const mor_subdomains* sd, const mor_basis_opts* 
   mor_bases_s& Bo = *bases;
   PlanScratch ps;
   int64_t not_conv = 0;
+  // the host plan of the next wave is built while the device works on the current one
+  auto plan_async = [&](int s0, HostPlan* out, std::string* err) {
+    const int s1 = std::min(g.n_sd, s0 + sd->wave_sd);
+    return std::async(std::launch::async, [=, &g, &ps] {
+      return build_wave_plan(g.n_nodes, g.n_tets, sd->h_tets.data(), sd->h_dir.data(),
+                             sd->h_xyz.data(), g, s0, s1, *out, ps, *err);
+    });
+  };
+  auto next_plan = std::make_unique<HostPlan>();
+  std::string next_err;
+  std::future<int> next = plan_async(0, next_plan.get(), &next_err);
   for (int s0 = 0; s0 < g.n_sd; s0 += sd->wave_sd) {
     const int s1 = std::min(g.n_sd, s0 + sd->wave_sd), nw = s1 - s0;
     auto W = std::make_unique<mor_subdomains_s>();
-    std::string err;
-    int rc = build_wave_plan(g.n_nodes, g.n_tets, sd->h_tets.data(), sd->h_dir.data(),
-                             sd->h_xyz.data(), g, s0, s1, W->hp, ps, err);
-    if (rc != MOR_OK) return fail(rc, err);
+    int rc = next.get();
+    if (rc != MOR_OK) return fail(rc, next_err);
+    W->hp = std::move(*next_plan);
+    if (s1 < g.n_sd) next = plan_async(s1, next_plan.get(), &next_err);
+    // a return below leaves the pending plan to be joined by the future's destructor
     W->xyz = sd->xyz;
     W->tets = sd->tets;
     W->kappa = sd->kappa;

@@ -46,24 +46,32 @@ def kuhn_cube(n: int, jitter: float = 0.0, seed: int = 0) -> Mesh:
 
     jitter > 0 moves every interior node by U(-jitter*h, jitter*h) per coordinate
     (seeded); the seed is rejected (ValueError) if any tetrahedron would invert.
+    Without jitter every cell is a translate of the first, so each of the 6 Kuhn
+    permutations is oriented once (int32 arrays throughout: the 440^3 cube has 5.1e8
+    tetrahedra).
     """
     h = 1.0 / n
     g = np.arange(n + 1, dtype=np.float64) * h
     z, y, x = np.meshgrid(g, g, g, indexing="ij")
     xyz = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+    del x, y, z
 
-    c = np.arange(n, dtype=np.int64)
+    c = np.arange(n, dtype=np.int32)
     cz, cy, cx = np.meshgrid(c, c, c, indexing="ij")
     cx, cy, cz = cx.ravel(), cy.ravel(), cz.ravel()
-    tets = np.empty((n ** 3, 6, 4), dtype=np.int64)
+    tets = np.empty((n ** 3, 6, 4), dtype=np.int32)
     for p, perm in enumerate(_PERMS):
-        off = np.zeros((4, 3), dtype=np.int64)
+        off = np.zeros((4, 3), dtype=np.int32)
         off[1, perm[0]] = 1
         off[2] = off[1]
         off[2, perm[1]] += 1
         off[3] = 1
+        col = [0, 1, 2, 3]
+        if jitter == 0.0 and np.linalg.det((off[1:] - off[0]).astype(np.float64)) < 0:
+            col = [0, 2, 1, 3]          # positive orientation: swap vertices 1 and 2
         for a in range(4):
-            tets[:, p, a] = node_id(cx + off[a, 0], cy + off[a, 1], cz + off[a, 2], n)
+            tets[:, p, col[a]] = node_id(cx + off[a, 0], cy + off[a, 1], cz + off[a, 2], n)
+    del cx, cy, cz
     tets = tets.reshape(-1, 4)
 
     ii = np.arange(n + 1)
@@ -76,18 +84,16 @@ def kuhn_cube(n: int, jitter: float = 0.0, seed: int = 0) -> Mesh:
         d = rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
         d[dirichlet.astype(bool)] = 0.0
         xyz = xyz + d
-
-    # orient every tetrahedron positively
-    e = xyz[tets[:, 1:]] - xyz[tets[:, :1]]
-    det = np.einsum("ti,ti->t", e[:, 0], np.cross(e[:, 1], e[:, 2]))
-    neg = det < 0
-    tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
-    if jitter > 0.0:
+        # orient every tetrahedron positively, then reject inverted ones
+        e = xyz[tets[:, 1:]] - xyz[tets[:, :1]]
+        det = np.einsum("ti,ti->t", e[:, 0], np.cross(e[:, 1], e[:, 2]))
+        neg = det < 0
+        tets[neg, 1], tets[neg, 2] = tets[neg, 2].copy(), tets[neg, 1].copy()
         e = xyz[tets[:, 1:]] - xyz[tets[:, :1]]
         det = np.einsum("ti,ti->t", e[:, 0], np.cross(e[:, 1], e[:, 2]))
         if np.any(det <= 0):
             raise ValueError("jitter seed inverts a tetrahedron; choose another seed")
-    return Mesh(n=n, xyz=np.ascontiguousarray(xyz), tets=tets.astype(np.int32),
+    return Mesh(n=n, xyz=np.ascontiguousarray(xyz), tets=np.ascontiguousarray(tets),
                 dirichlet=dirichlet)
 
 
