@@ -115,41 +115,51 @@ void make_tiles(const std::vector<int64_t>& begin, const std::vector<int64_t>& e
   }
 }
 
+// Pack the rows of all subdomains into one sliced-ELL pattern and incidence CSR.  Row
+// lengths and incidence offsets come first (prefix sums), then every subdomain writes
+// its own contiguous rows in parallel; a slice may straddle two subdomains, so slice
+// widths are a separate pass over the row lengths.
 void pack_ell(const std::vector<SubOut>& outs, bool plus, const std::vector<int64_t>& off,
               int64_t n_rows, HostEll& E, std::vector<int64_t>& inc_ptr,
-              std::vector<int32_t>& inc_tet, std::vector<uint32_t>& inc_code) {
-  int32_t W = 0;
-  for (auto& o : outs) {
-    const LocalRows& R = plus ? o.P : o.W;
-    for (size_t r = 0; r + 1 < R.ptr.size(); ++r)
-      W = std::max<int32_t>(W, (int32_t)(R.ptr[r + 1] - R.ptr[r]));
+              std::vector<int32_t>& inc_tet, std::vector<uint32_t>& inc_code, int n_threads) {
+  const int n_sd = (int)outs.size();
+  std::vector<int32_t> len(n_rows, 0);
+  inc_ptr.assign(n_rows + 1, 0);
+  for (int i = 0; i < n_sd; ++i) {
+    const LocalRows& R = plus ? outs[i].P : outs[i].W;
+    for (size_t r = 0; r + 1 < R.ptr.size(); ++r) {
+      len[off[i] + r] = (int32_t)(R.ptr[r + 1] - R.ptr[r]);
+      inc_ptr[off[i] + r + 1] = R.inc_ptr[r + 1] - R.inc_ptr[r];
+    }
   }
-  int64_t n_slices = (n_rows + kSlice - 1) / kSlice;
+  for (int64_t r = 0; r < n_rows; ++r) inc_ptr[r + 1] += inc_ptr[r];
+  int32_t W = 0;
+  for (int64_t r = 0; r < n_rows; ++r) W = std::max(W, len[r]);
+  const int64_t n_slices = (n_rows + kSlice - 1) / kSlice;
   E.n_rows = n_rows;
   E.W = W;
   E.width.assign(n_slices, 0);
+  for (int64_t r = 0; r < n_rows; ++r)
+    E.width[r / kSlice] = std::max(E.width[r / kSlice], len[r]);
   E.col.assign(n_slices * kSlice * (int64_t)W, -1);
-  inc_ptr.assign(n_rows + 1, 0);
-  inc_tet.clear();
-  inc_code.clear();
-  for (size_t i = 0; i < outs.size(); ++i) {
+  inc_tet.assign(inc_ptr[n_rows], 0);
+  inc_code.assign(inc_ptr[n_rows], 0);
+  parallel_for(n_sd, n_threads, [&](int i, int) {
     const LocalRows& R = plus ? outs[i].P : outs[i].W;
-    int64_t nr = (int64_t)R.ptr.size() - 1;
+    const int64_t nr = (int64_t)R.ptr.size() - 1;
     for (int64_t r = 0; r < nr; ++r) {
-      int64_t row = off[i] + r;
-      int64_t len = R.ptr[r + 1] - R.ptr[r];
-      int64_t s = row / kSlice;
-      E.width[s] = std::max<int32_t>(E.width[s], (int32_t)len);
-      for (int64_t j = 0; j < len; ++j)
+      const int64_t row = off[i] + r, s = row / kSlice;
+      const int64_t l = R.ptr[r + 1] - R.ptr[r];
+      for (int64_t j = 0; j < l; ++j)
         E.col[s * kSlice * W + j * kSlice + (row % kSlice)] =
             (int32_t)(off[i] + R.cols[R.ptr[r] + j]);
-      for (int64_t q = R.inc_ptr[r]; q < R.inc_ptr[r + 1]; ++q) {
-        inc_tet.push_back(R.inc_tet[q]);
-        inc_code.push_back(R.inc_code[q]);
+      int64_t q = inc_ptr[row];
+      for (int64_t k = R.inc_ptr[r]; k < R.inc_ptr[r + 1]; ++k, ++q) {
+        inc_tet[q] = R.inc_tet[k];
+        inc_code[q] = R.inc_code[k];
       }
-      inc_ptr[row + 1] = (int64_t)inc_tet.size();
     }
-  }
+  });
 }
 
 // spread the low 10 bits of v to every third bit
@@ -525,8 +535,10 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
       hp.o_sd[o0 + o] = i;
     }
   }
-  pack_ell(outs, true, hp.Poff, hp.nP, hp.pat_P, hp.incP_ptr, hp.incP_tet, hp.incP_code);
-  pack_ell(outs, false, hp.Woff, hp.nW, hp.pat_W, hp.incW_ptr, hp.incW_tet, hp.incW_code);
+  pack_ell(outs, true, hp.Poff, hp.nP, hp.pat_P, hp.incP_ptr, hp.incP_tet, hp.incP_code,
+           nthr);
+  pack_ell(outs, false, hp.Woff, hp.nW, hp.pat_W, hp.incW_ptr, hp.incW_tet, hp.incW_code,
+           nthr);
   if (hp.pat_P.W >= (int32_t)kNoSlot || hp.pat_W.W >= (int32_t)kNoSlot) {
     err = "mor_build_subdomains: node degree too large for the incidence code";
     return MOR_ERR_BAD_MESH;
