@@ -31,6 +31,7 @@ void parallel_for(int n, int n_threads, F f) {
 struct Scratch {
   std::vector<int32_t> ball, vert, loc_mark, loc, wmark, wloc;
   std::vector<uint8_t> tplus, tomega;
+  std::vector<int32_t> seen, slot_of;  // build_rows work arrays
   void init(int64_t n_nodes, int64_t n_tets) {
     ball.assign(n_nodes, 0);
     vert.assign(n_nodes, 0);
@@ -59,11 +60,37 @@ struct SubOut {
   std::string err;
 };
 
+// Sort ids whose flags are set: a scan of the flag array over their range when that range
+// is short (a few times the count, as for compact subdomains), else a comparison sort.
+void sort_flagged(std::vector<int32_t>& ids, const std::vector<uint8_t>& flag) {
+  if (ids.empty()) return;
+  int32_t lo = INT32_MAX, hi = -1;
+  for (int32_t e : ids) {
+    lo = std::min(lo, e);
+    hi = std::max(hi, e);
+  }
+  if ((int64_t)hi - lo + 1 <= 16 * (int64_t)ids.size()) {
+    ids.clear();
+    for (int32_t e = lo; e <= hi; ++e)
+      if (flag[e]) ids.push_back(e);
+  } else {
+    std::sort(ids.begin(), ids.end());
+  }
+}
+
+// Rows of one local space (row_nodes in local order): the sorted local columns of every
+// row (nodes sharing an element of tflag with it) and its incidence entries.  seen and
+// slot_of are work arrays over the local indices: seen dedupes a row's candidates
+// (stamped with a per-call row counter), slot_of maps a local column to its slot.
 void build_rows(const std::vector<int32_t>& row_nodes, const int32_t* tets,
                 const std::vector<int64_t>& n2t_ptr, const std::vector<int32_t>& n2t,
                 const std::vector<uint8_t>& tflag, const std::vector<int32_t>& mark,
-                const std::vector<int32_t>& loc, int32_t stamp, LocalRows& R) {
+                const std::vector<int32_t>& loc, int32_t stamp, LocalRows& R,
+                std::vector<int32_t>& seen, std::vector<int32_t>& slot_of) {
+  seen.assign(row_nodes.size(), -1);
+  if (slot_of.size() < row_nodes.size()) slot_of.resize(row_nodes.size());
   std::vector<int32_t> cand;
+  int32_t row = 0;
   for (int32_t g : row_nodes) {
     cand.clear();
     for (int64_t q = n2t_ptr[g]; q < n2t_ptr[g + 1]; ++q) {
@@ -71,11 +98,16 @@ void build_rows(const std::vector<int32_t>& row_nodes, const int32_t* tets,
       if (!tflag[e]) continue;
       for (int b = 0; b < 4; ++b) {
         int32_t vb = tets[4 * (int64_t)e + b];
-        if (mark[vb] == stamp) cand.push_back(loc[vb]);
+        if (mark[vb] != stamp) continue;
+        int32_t l = loc[vb];
+        if (seen[l] != row) {
+          seen[l] = row;
+          cand.push_back(l);
+        }
       }
     }
     std::sort(cand.begin(), cand.end());
-    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    for (size_t k = 0; k < cand.size(); ++k) slot_of[cand[k]] = (int32_t)k;
     R.cols.insert(R.cols.end(), cand.begin(), cand.end());
     R.ptr.push_back((int64_t)R.cols.size());
     for (int64_t q = n2t_ptr[g]; q < n2t_ptr[g + 1]; ++q) {
@@ -85,17 +117,14 @@ void build_rows(const std::vector<int32_t>& row_nodes, const int32_t* tets,
       for (int b = 0; b < 4; ++b) {
         int32_t vb = tets[4 * (int64_t)e + b];
         if (vb == g) code |= (uint32_t)b;
-        uint32_t slot = kNoSlot;
-        if (mark[vb] == stamp) {
-          auto it = std::lower_bound(cand.begin(), cand.end(), loc[vb]);
-          slot = (uint32_t)(it - cand.begin());
-        }
+        uint32_t slot = mark[vb] == stamp ? (uint32_t)slot_of[loc[vb]] : kNoSlot;
         code |= slot << (2 + 7 * b);
       }
       R.inc_tet.push_back(e);
       R.inc_code.push_back(code);
     }
     R.inc_ptr.push_back((int64_t)R.inc_tet.size());
+    ++row;
   }
 }
 
@@ -393,7 +422,7 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
           }
       frontier.swap(next);
     }
-    // T_i^+ = elements touching the ball
+    // T_i^+ = elements touching the ball, ascending
     for (int32_t v : ball_list)
       for (int64_t q = n2t_ptr[v]; q < n2t_ptr[v + 1]; ++q) {
         int32_t e = n2t[q];
@@ -402,7 +431,7 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
           ss.plus_tets.push_back(e);
         }
       }
-    std::sort(ss.plus_tets.begin(), ss.plus_tets.end());
+    sort_flagged(ss.plus_tets, S.tplus);
     // nodes of T_i^+: interior (all elements in T_i^+) -> I, others -> B
     for (int32_t e : ss.plus_tets)
       for (int b = 0; b < 4; ++b) {
@@ -417,7 +446,7 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
       }
     std::sort(ss.I.begin(), ss.I.end());
     std::sort(ss.B.begin(), ss.B.end());
-    // omega_i = elements touching P_i
+    // omega_i = elements touching P_i, ascending
     for (int32_t v : g.Pown[i])
       for (int64_t q = n2t_ptr[v]; q < n2t_ptr[v + 1]; ++q) {
         int32_t e = n2t[q];
@@ -426,7 +455,7 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
           ss.omega_tets.push_back(e);
         }
       }
-    std::sort(ss.omega_tets.begin(), ss.omega_tets.end());
+    sort_flagged(ss.omega_tets, S.tomega);
     for (int32_t e : ss.omega_tets)
       for (int b = 0; b < 4; ++b) {
         int32_t v = tets[4 * (int64_t)e + b];
@@ -462,8 +491,10 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     if (so.err.empty()) {
       std::vector<int32_t> prow(ss.Ip);
       prow.insert(prow.end(), ss.Bp.begin(), ss.Bp.end());
-      build_rows(prow, tets, n2t_ptr, n2t, S.tplus, S.loc_mark, S.loc, st, so.P);
-      build_rows(ss.omega, tets, n2t_ptr, n2t, S.tomega, S.wmark, S.wloc, st, so.W);
+      build_rows(prow, tets, n2t_ptr, n2t, S.tplus, S.loc_mark, S.loc, st, so.P, S.seen,
+                 S.slot_of);
+      build_rows(ss.omega, tets, n2t_ptr, n2t, S.tomega, S.wmark, S.wloc, st, so.W, S.seen,
+                 S.slot_of);
     }
     // clear the element flags for the next subdomain on this thread
     for (int32_t e : ss.plus_tets) S.tplus[e] = 0;
