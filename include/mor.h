@@ -260,6 +260,18 @@ int mor_lift(const mor_subdomains* sd, const mor_bases* b, const double* x_dev,
 int mor_energy_norm(const mor_subdomains* sd, const double* u1_dev, const double* u2_dev,
                     double* out, void* stream);
 
+/* Host-only check of step 1 (no device needed; mesh arrays on the host, xyz may be
+ * NULL): builds the one-shot plan of mor_build_subdomains, the global plan and the
+ * waves of wave_subdomains of mor_build_subdomains_streamed, and the coarse-level
+ * aggregates for coarse_rows.  out[host, 8] = {n_sub, extended rows, waves, wave rows /
+ * patterns / incidences / maps that differ from the one-shot plan, aggregate violations
+ * (not contiguous, not I-then-B, above the cap), most aggregates meeting one row tile,
+ * most aggregates of one subdomain, owned DOFs}.  The paper has no counterpart. */
+int mor_debug_plan_check(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
+                         const uint8_t* dirichlet, const int32_t* owner, const double* xyz,
+                         int32_t r_hops, int32_t wave_subdomains, int32_t coarse_rows,
+                         int64_t* out);
+
 /* Debug/parity access: the field-sketch right-hand side L xi of subdomain `sub`
  * (rows I then B, k columns, row-major) into out[host, (|I|+|B|) x k], computed by the
  * same kernel mor_build_bases uses (binary32 Gaussian draws, binary64 element factors

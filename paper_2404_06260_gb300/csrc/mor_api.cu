@@ -1274,6 +1274,82 @@ int mor_energy_norm(const mor_subdomains* sd, const double* u1_dev, const double
   return MOR_OK;
 }
 
+int mor_debug_plan_check(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
+                         const uint8_t* dirichlet, const int32_t* owner, const double* xyz,
+                         int32_t r_hops, int32_t wave_subdomains, int32_t coarse_rows,
+                         int64_t* out) {
+  if (!tets || !dirichlet || !owner || !out || wave_subdomains < 1 || coarse_rows < 1)
+    return fail(MOR_ERR_ARG, "mor_debug_plan_check: bad argument");
+  std::string err;
+  HostPlan full, g;
+  int rc = build_host_plan(n_nodes, n_tets, tets, dirichlet, owner, r_hops, xyz, full, err);
+  if (rc != MOR_OK) return fail(rc, err);
+  rc = build_global_plan(n_nodes, n_tets, tets, dirichlet, owner, r_hops, g, err);
+  if (rc != MOR_OK) return fail(rc, err);
+  int64_t bad = 0, waves = 0;
+  if (g.nO != full.nO || g.o_node != full.o_node || g.o_sd != full.o_sd ||
+      g.pair_ptr != full.pair_ptr || g.e_urow != full.e_urow || g.e_vrow != full.e_vrow)
+    ++bad;
+  PlanScratch ps;
+  for (int s0 = 0; s0 < g.n_sd; s0 += wave_subdomains, ++waves) {
+    const int s1 = std::min(g.n_sd, s0 + wave_subdomains);
+    HostPlan w;
+    rc = build_wave_plan(n_nodes, n_tets, tets, dirichlet, xyz, g, s0, s1, w, ps, err);
+    if (rc != MOR_OK) return fail(rc, err);
+    const int64_t P0 = full.Poff[s0], W0 = full.Woff[s0], O0 = full.Ooff[s0];
+    if (w.nP != full.Poff[s1] - P0 || w.nW != full.Woff[s1] - W0 ||
+        w.nO != full.Ooff[s1] - O0) {
+      ++bad;
+      continue;
+    }
+    for (int64_t r = 0; r < w.nP; ++r) {
+      if (w.p_node[r] != full.p_node[P0 + r] || w.p_code[r] != full.p_code[P0 + r]) ++bad;
+      const int64_t sw = r / kSlice, sf = (P0 + r) / kSlice;
+      for (int j = 0; j < std::max(w.pat_P.W, full.pat_P.W); ++j) {
+        int32_t cw = j < w.pat_P.width[sw] ? w.pat_P.col[(sw * kSlice + 0) * w.pat_P.W +
+                                                         j * kSlice + r % kSlice] : -1;
+        int32_t cf = j < full.pat_P.width[sf]
+                         ? full.pat_P.col[sf * kSlice * full.pat_P.W + j * kSlice +
+                                          (P0 + r) % kSlice]
+                         : -1;
+        if ((cw < 0) != (cf < 0) || (cf >= 0 && cf != cw + P0)) ++bad;
+      }
+      for (int64_t q = w.incP_ptr[r], qf = full.incP_ptr[P0 + r]; q < w.incP_ptr[r + 1];
+           ++q, ++qf)
+        if (w.incP_tet[q] != full.incP_tet[qf] || w.incP_code[q] != full.incP_code[qf]) ++bad;
+    }
+    for (int64_t x = 0; x < w.nW; ++x)
+      if (w.w2p[x] + P0 != full.w2p[W0 + x]) ++bad;
+    for (int64_t o = 0; o < w.nO; ++o)
+      if (w.o_node[o] != full.o_node[O0 + o] || w.o2w[o] + W0 != full.o2w[O0 + o]) ++bad;
+  }
+  // aggregates of the coarse level: contiguous, ordered I then B, within the caps
+  AggPlan ap;
+  build_aggregates(full, coarse_rows, kMaxAgg, ap);
+  int64_t agg_bad = 0, max_nc = 0;
+  for (int i = 0; i < full.n_sd; ++i) {
+    const int n0 = ap.nca[0][i], n1 = ap.nca[1][i];
+    max_nc = std::max<int64_t>(max_nc, n1);
+    if (n1 > kMaxAgg || n0 > n1) ++agg_bad;
+    const int32_t* al = ap.aloc.data() + full.Poff[i];
+    const int nrow = full.nI[i] + full.nB[i];
+    for (int l = 0; l < nrow; ++l) {
+      if (al[l] < 0 || al[l] >= n1) ++agg_bad;
+      if (l > 0 && (al[l] < al[l - 1] || al[l] > al[l - 1] + 1)) ++agg_bad;
+      if ((l < full.nI[i]) != (al[l] < n0)) ++agg_bad;
+    }
+  }
+  out[0] = full.n_sd;
+  out[1] = full.nP;
+  out[2] = waves;
+  out[3] = bad;
+  out[4] = agg_bad;
+  out[5] = ap.max_slots;
+  out[6] = max_nc;
+  out[7] = full.nO;
+  return MOR_OK;
+}
+
 int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, int32_t sub,
                          double* out, void* stream) {
   if (!sd || !opts || !out || sub < 0 || sub >= sd->hp.n_sd)

@@ -58,6 +58,7 @@ def _sig(name, res, *args):
 _sig("mor_build_subdomains", _i32, ctypes.POINTER(_MeshC), _P, _i32, _P, ctypes.POINTER(_P))
 _sig("mor_build_subdomains_streamed", _i32, ctypes.POINTER(_MeshC), _P, _i32, _i32, _P,
      ctypes.POINTER(_P))
+_sig("mor_debug_plan_check", _i32, _i64, _i64, _P, _P, _P, _P, _i32, _i32, _i32, _P)
 _sig("mor_subdomains_counts", _i32, _P, ctypes.POINTER(_i32), _P)
 _sig("mor_subdomains_indices", _i32, _P, _i32, _i32, _P)
 _sig("mor_basis_opts_default", _i32, ctypes.POINTER(BasisOpts))
@@ -92,7 +93,8 @@ EXPORTED = ["mor_build_subdomains", "mor_build_subdomains_streamed", "mor_subdom
             "mor_bases_get_Q", "mor_bases_get_bt", "mor_bases_stats", "mor_project",
             "mor_reduced_info", "mor_reduced_dense", "mor_solve_reduced",
             "mor_solve_reduced_noalloc", "mor_lift",
-            "mor_energy_norm", "mor_debug_sketch_rhs", "mor_profile_enable",
+            "mor_energy_norm", "mor_debug_sketch_rhs", "mor_debug_plan_check",
+            "mor_profile_enable",
             "mor_profile_reset", "mor_profile_query", "mor_kernel_launches", "mor_free_subdomains",
             "mor_free_bases", "mor_free_reduced", "mor_last_error"]
 
@@ -321,3 +323,18 @@ def kernel_launches() -> int:
     out = _i64()
     _check(_lib.mor_kernel_launches(ctypes.byref(out)))
     return out.value
+
+
+def plan_check(mesh, owner, r_hops: int, wave: int, coarse_rows: int = 100) -> dict:
+    """Host-only consistency check of step 1 (mor_debug_plan_check); needs no GPU."""
+    tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
+    dirichlet = np.ascontiguousarray(mesh.dirichlet, dtype=np.uint8)
+    own = np.ascontiguousarray(owner, dtype=np.int32)
+    xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    out = np.zeros(8, dtype=np.int64)
+    _check(_lib.mor_debug_plan_check(int(mesh.n_nodes), int(mesh.n_tets), _ptr(tets),
+                                     _ptr(dirichlet), _ptr(own), _ptr(xyz), int(r_hops),
+                                     int(wave), int(coarse_rows), _ptr(out)))
+    keys = ["n_sub", "rows", "waves", "wave_mismatches", "aggregate_violations",
+            "max_slots", "max_aggregates", "owned"]
+    return dict(zip(keys, out.tolist()))
