@@ -208,7 +208,7 @@ template <typename T>
 __device__ __forceinline__ Pack<T> spmm_row(int rr, int w, int W, int tx, const int32_t* scol,
                                             const T* sval, const T* __restrict__ X, int kp) {
   constexpr int N = Pack<T>::N;
-  constexpr int U = 8;
+  constexpr int U = 2;
   Pack<T> acc;
 #pragma unroll
   for (int e = 0; e < N; ++e) acc.v[e] = T(0);
