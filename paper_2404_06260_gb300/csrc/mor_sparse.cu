@@ -42,15 +42,23 @@ __device__ __forceinline__ Geo geo() {
   return g;
 }
 
+// two consecutive slots of one row of a staged sliced-ELL tile: values first, so that a
+// binary32 record is one 16-byte shared-memory load
+template <typename T>
+struct alignas(16) Slot2 {
+  T v[2];
+  int32_t c[2];
+};
+
 // shared memory layout: red[nth * N] of T, scratch[nth] doubles, sums[2*kp] doubles,
-// then the staged sliced-ELL tile: scol[kTileRows * W] int32, sval[kTileRows * W] T
+// then the staged sliced-ELL tile: slots[((W + 1) / 2) * kTileRows] pair records,
+// pair-major (record h of row rr at h * kTileRows + rr)
 template <typename T>
 struct Smem {
   T* red;
   double* scratch;
   double* sums;
-  int32_t* scol;
-  T* sval;
+  Slot2<T>* slots;
 };
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 template <typename T>
@@ -63,16 +71,14 @@ __device__ __forceinline__ Smem<T> smem_layout(const Geo& g, int kp, int W) {
   s.scratch = reinterpret_cast<double*>(raw + o);
   s.sums = s.scratch + g.nth;
   o += align16(sizeof(double) * ((size_t)g.nth + 2 * kp));
-  s.scol = reinterpret_cast<int32_t*>(raw + o);
-  o += align16(sizeof(int32_t) * (size_t)kTileRows * W);
-  s.sval = reinterpret_cast<T*>(raw + o);
+  s.slots = reinterpret_cast<Slot2<T>*>(raw + o);
   return s;
 }
 template <typename T>
 __host__ __device__ __forceinline__ size_t smem_bytes(int nch, int rb, int kp, int W) {
   size_t nth = (size_t)nch * rb;
   return align16(16 * nth) + align16(sizeof(double) * (nth + 2 * kp)) +
-         align16(sizeof(int32_t) * (size_t)kTileRows * W) + sizeof(T) * (size_t)kTileRows * W;
+         sizeof(Slot2<T>) * (size_t)kTileRows * ((W + 1) / 2);
 }
 
 // column sums over ty of per-thread N-wide accumulators -> out[tx*N + e] (double)
@@ -172,67 +178,70 @@ __device__ __forceinline__ void count_active(const Geo& g, const int* done, int 
 // ---------------------------------------------------------------------------------
 // Sliced-ELL products on a row tile.  The tile's slots (column index and value) are
 // first staged in shared memory with coalesced loads (consecutive threads take
-// consecutive rows of one slot), which takes the index load off the critical path of
-// the gathers.  Thread (tx, ty) then computes the 16-byte column chunk tx of rows
-// ty, ty + RB, ...: eight slots are gathered (predicated, independent loads) before
-// their multiply-adds.  k_spmm: Y = A X.  k_cg_spmm_pq: q = A p with the column sums
-// of p.q.  k_residual64: r = b - A x with the column sums of r.r.
+// consecutive rows of one slot pair), which takes the index load off the critical path
+// of the gathers; a row's slots 2h and 2h + 1 form one record, so one shared load feeds
+// two gathers.  Thread (tx, ty) then computes the 16-byte column chunk tx of rows
+// ty, ty + RB, ...: the slots of a batch are gathered (predicated, independent loads)
+// before their multiply-adds, which run in slot order.  k_spmm: Y = A X.
+// k_cg_spmm_pq: q = A p with the column sums of p.q.  k_residual64: r = b - A x with
+// the column sums of r.r.
 template <typename T>
 __device__ __forceinline__ void stage_tile(const Geo& g, int r0, int nrows,
-                                           const EllView<T>& A, int32_t* scol, T* sval) {
-  const int W = A.W;
-  const bool full = nrows == kTileRows;  // full tiles: slot and row by shifts
-  for (int idx = g.tid; idx < nrows * W; idx += g.nth) {
-    int j, rr;
+                                           const EllView<T>& A, Slot2<T>* slots) {
+  const int W = A.W, W2 = (W + 1) / 2;
+  const bool full = nrows == kTileRows;  // full tiles: pair and row by shifts
+  for (int idx = g.tid; idx < nrows * W2; idx += g.nth) {
+    int h, rr;
     if (full) {
-      j = idx / kTileRows;  // kTileRows is a power of two: compiles to a shift
+      h = idx / kTileRows;  // kTileRows is a power of two: compiles to a shift
       rr = idx & (kTileRows - 1);
     } else {
-      j = idx / nrows;
-      rr = idx - j * nrows;
+      h = idx / nrows;
+      rr = idx - h * nrows;
     }
     int64_t r = (int64_t)r0 + rr;
-    int32_t c = -1;
-    T v = T(0);
-    if (j < A.width[r >> 5]) {
-      int64_t at = ell_at(r, j, W);
-      c = A.col[at];
-      v = A.val[at];
+    const int w = A.width[r >> 5];
+    Slot2<T> rec;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int j = 2 * h + u;
+      rec.c[u] = -1;
+      rec.v[u] = T(0);
+      if (j < w) {
+        int64_t at = ell_at(r, j, W);
+        rec.c[u] = A.col[at];
+        rec.v[u] = A.val[at];
+      }
     }
-    scol[rr * W + j] = c;
-    sval[rr * W + j] = v;
+    slots[h * kTileRows + rr] = rec;
   }
 }
 
+// row rr of the staged tile (slice width w) times X: column chunk tx
 template <typename T>
-__device__ __forceinline__ Pack<T> spmm_row(int rr, int w, int W, int tx, const int32_t* scol,
-                                            const T* sval, const T* __restrict__ X, int kp) {
+__device__ __forceinline__ Pack<T> spmm_row(int rr, int w, int tx, const Slot2<T>* slots,
+                                            const T* __restrict__ X, int kp) {
   constexpr int N = Pack<T>::N;
-  constexpr int U = 2;
   Pack<T> acc;
 #pragma unroll
   for (int e = 0; e < N; ++e) acc.v[e] = T(0);
-  const int32_t* cr = scol + rr * W;
-  const T* vr = sval + rr * W;
-  for (int j0 = 0; j0 < w; j0 += U) {
-    Pack<T> xv[U];
-    T av[U];
+  const int w2 = (w + 1) >> 1;
+  for (int h = 0; h < w2; ++h) {
+    const Slot2<T> rec = slots[h * kTileRows + rr];
+    Pack<T> xv[2];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int j = j0 + u;
-      int32_t c = (j < w) ? cr[j] : -1;
-      av[u] = (j < w) ? vr[j] : T(0);
-      if (c >= 0) {
-        xv[u] = ld(X + (int64_t)c * kp + tx * N);
+    for (int u = 0; u < 2; ++u) {
+      if (rec.c[u] >= 0) {
+        xv[u] = ld(X + (int64_t)rec.c[u] * kp + tx * N);
       } else {
 #pragma unroll
         for (int e = 0; e < N; ++e) xv[u].v[e] = T(0);
       }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < 2; ++u)
 #pragma unroll
-      for (int e = 0; e < N; ++e) acc.v[e] += av[u] * xv[u].v[e];
+      for (int e = 0; e < N; ++e) acc.v[e] += rec.v[u] * xv[u].v[e];
   }
   return acc;
 }
@@ -245,42 +254,50 @@ __global__ void k_spmm(DTiles tl, EllView<T> A, const T* __restrict__ X, T* __re
   Smem<T> sm = smem_layout<T>(g, kp, A.W);
   const int tile = blockIdx.x;
   const int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
+  stage_tile(g, r0, r1 - r0, A, sm.slots);
   __syncthreads();
   for (int rr = g.ty; rr < r1 - r0; rr += g.rb) {
     int64_t row = r0 + rr;
     st(Y + row * kp + g.tx * N,
-       spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, X, kp));
+       spmm_row(rr, A.width[row >> 5], g.tx, sm.slots, X, kp));
   }
 }
 
 // binary64 residual row: A x and sum_j |a_ij x_j| in one pass over the staged slots
-__device__ __forceinline__ void spmm_row_res(int rr, int w, int W, int tx, const int32_t* scol,
-                                             const double* sval, const double* __restrict__ X,
-                                             int kp, Pack<double>& acc, Pack<double>& aabs) {
+// (batches of four records, eight slots)
+__device__ __forceinline__ void spmm_row_res(int rr, int w, int tx, const Slot2<double>* slots,
+                                             const double* __restrict__ X, int kp,
+                                             Pack<double>& acc, Pack<double>& aabs) {
   constexpr int N = Pack<double>::N;
-  constexpr int U = 8;
+  constexpr int H = 4;
 #pragma unroll
   for (int e = 0; e < N; ++e) acc.v[e] = aabs.v[e] = 0.0;
-  const int32_t* cr = scol + rr * W;
-  const double* vr = sval + rr * W;
-  for (int j0 = 0; j0 < w; j0 += U) {
-    Pack<double> xv[U];
-    double av[U];
+  const int w2 = (w + 1) >> 1;
+  for (int h0 = 0; h0 < w2; h0 += H) {
+    Pack<double> xv[2 * H];
+    double av[2 * H];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int j = j0 + u;
-      int32_t c = (j < w) ? cr[j] : -1;
-      av[u] = (j < w) ? vr[j] : 0.0;
-      if (c >= 0) {
-        xv[u] = ld(X + (int64_t)c * kp + tx * N);
+    for (int hh = 0; hh < H; ++hh) {
+      Slot2<double> rec;
+      if (h0 + hh < w2) {
+        rec = slots[(h0 + hh) * kTileRows + rr];
       } else {
+        rec.c[0] = rec.c[1] = -1;
+        rec.v[0] = rec.v[1] = 0.0;
+      }
 #pragma unroll
-        for (int e = 0; e < N; ++e) xv[u].v[e] = 0.0;
+      for (int u = 0; u < 2; ++u) {
+        av[2 * hh + u] = rec.v[u];
+        if (rec.c[u] >= 0) {
+          xv[2 * hh + u] = ld(X + (int64_t)rec.c[u] * kp + tx * N);
+        } else {
+#pragma unroll
+          for (int e = 0; e < N; ++e) xv[2 * hh + u].v[e] = 0.0;
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < 2 * H; ++u)
 #pragma unroll
       for (int e = 0; e < N; ++e) {
         double t = av[u] * xv[u].v[e];
@@ -290,8 +307,9 @@ __device__ __forceinline__ void spmm_row_res(int rr, int w, int W, int tx, const
   }
 }
 
+// at most 256 threads (kp <= 80 columns): 40 registers leave room for six blocks per SM
 template <typename T>
-__global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
+__global__ void __launch_bounds__(256, 6) k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
                              T* __restrict__ q, int kp, CgState s) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
@@ -299,7 +317,7 @@ __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
   const int tile = blockIdx.x, sd = tl.sd[tile];
   if (s.active[sd] == 0) return;  // every column of this subdomain has converged
   const int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
+  stage_tile(g, r0, r1 - r0, A, sm.slots);
   __syncthreads();
   T acc[N];
 #pragma unroll
@@ -307,7 +325,7 @@ __global__ void k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
   const int rend = pack_done<T>(s, sd, kp, g.tx) ? 0 : r1 - r0;
   for (int rr = g.ty; rr < rend; rr += g.rb) {
     int64_t row = r0 + rr;
-    Pack<T> qv = spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, p, kp);
+    Pack<T> qv = spmm_row(rr, A.width[row >> 5], g.tx, sm.slots, p, kp);
     int64_t o = row * kp + g.tx * N;
     st(q + o, qv);
     Pack<T> pv = ld(p + o);
@@ -344,7 +362,7 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
   Smem<double> sm = smem_layout<double>(g, kp, A.W);
   const int tile = blockIdx.x, sd = tl.sd[tile];
   const int r0 = tl.r0[tile], r1 = tl.r1[tile];
-  stage_tile(g, r0, r1 - r0, A, sm.scol, sm.sval);
+  stage_tile(g, r0, r1 - r0, A, sm.slots);
   __syncthreads();
   double acc[N] = {0.0, 0.0}, aca[N] = {0.0, 0.0}, axx[N] = {0.0, 0.0};
   for (int rr = g.ty; rr < r1 - r0; rr += g.rb) {
@@ -356,9 +374,9 @@ __global__ void k_residual64(DTiles tl, EllView<double> A, const double* __restr
       for (int e = 0; e < N; ++e) axx[e] += xo.v[e] * xo.v[e];
     }
     if constexpr (kFloor)
-      spmm_row_res(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, x, kp, ax, aabs);
+      spmm_row_res(rr, A.width[row >> 5], g.tx, sm.slots, x, kp, ax, aabs);
     else
-      ax = spmm_row(rr, A.width[row >> 5], A.W, g.tx, sm.scol, sm.sval, x, kp);
+      ax = spmm_row(rr, A.width[row >> 5], g.tx, sm.slots, x, kp);
     int64_t o = row * kp + g.tx * N;
     Pack<double> bv = ld(b + o), rv;
 #pragma unroll
@@ -561,7 +579,7 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r,
 // x += alpha p, r -= alpha q; ||r||^2, the fine r.z = r.D^{-1}r and the restriction of
 // the new r; the coarse kernel (STEP) completes r.M^{-1}r, beta and the done flags
 template <typename T>
-__global__ void k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
                                const T* __restrict__ q, const T* __restrict__ dinv, int kp,
                                CgState s, Coarse<T> co) {
   constexpr int N = Pack<T>::N;
@@ -770,7 +788,7 @@ __global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s,
 // p = gam (D^{-1} r + Z y_c) + beta p (p is not read where beta = 0), and p.r of the
 // new direction for the next step length
 template <typename T>
-__global__ void k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p,
                               const T* __restrict__ dinv, int kp, CgState s, Coarse<T> co) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
