@@ -309,8 +309,9 @@ __device__ __forceinline__ void spmm_row_res(int rr, int w, int tx, const Slot2<
 
 // at most 256 threads (kp <= 80 columns): 40 registers leave room for six blocks per SM
 template <typename T>
-__global__ void __launch_bounds__(256, 6) k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p,
-                             T* __restrict__ q, int kp, CgState s) {
+__global__ void __launch_bounds__(256, 6)
+    k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p, T* __restrict__ q, int kp,
+                 CgState s) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, A.W);
@@ -577,11 +578,12 @@ __global__ void k_cg_init(DTiles tl, const T* __restrict__ b, T* x, T* r,
 }
 
 // x += alpha p, r -= alpha q; ||r||^2, the fine r.z = r.D^{-1}r and the restriction of
-// the new r; the coarse kernel (STEP) completes r.M^{-1}r, beta and the done flags
+// the new r; the coarse kernel (STEP) completes r.M^{-1}r, beta and the done flags.
+// 48 registers (binary32) leave room for five blocks per SM; six cost spills.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4) k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p,
-                               const T* __restrict__ q, const T* __restrict__ dinv, int kp,
-                               CgState s, Coarse<T> co) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4)
+    k_cg_update_xr(DTiles tl, T* x, T* r, const T* __restrict__ p, const T* __restrict__ q,
+                   const T* __restrict__ dinv, int kp, CgState s, Coarse<T> co) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
@@ -788,8 +790,9 @@ __global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s,
 // p = gam (D^{-1} r + Z y_c) + beta p (p is not read where beta = 0), and p.r of the
 // new direction for the next step length
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4) k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p,
-                              const T* __restrict__ dinv, int kp, CgState s, Coarse<T> co) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 4)
+    k_cg_update_p(DTiles tl, const T* __restrict__ r, T* p, const T* __restrict__ dinv, int kp,
+                  CgState s, Coarse<T> co) {
   constexpr int N = Pack<T>::N;
   Geo g = geo();
   Smem<T> sm = smem_layout<T>(g, kp, 0);
