@@ -103,8 +103,8 @@ struct Allocs {
     }
     return MOR_OK;
   }
-  template <class T>
-  int upload(T** p, const std::vector<T>& h, cudaStream_t st) {
+  template <class T, class Al>
+  int upload(T** p, const std::vector<T, Al>& h, cudaStream_t st) {
     TRY(alloc(p, h.size(), false));
     if (!h.empty()) {
       cudaError_t e = cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T),

@@ -150,7 +150,7 @@ void make_tiles(const std::vector<int64_t>& begin, const std::vector<int64_t>& e
 // widths are a separate pass over the row lengths.
 void pack_ell(const std::vector<SubOut>& outs, bool plus, const std::vector<int64_t>& off,
               int64_t n_rows, HostEll& E, std::vector<int64_t>& inc_ptr,
-              std::vector<int32_t>& inc_tet, std::vector<uint32_t>& inc_code, int n_threads) {
+              BigVec<int32_t>& inc_tet, BigVec<uint32_t>& inc_code, int n_threads) {
   const int n_sd = (int)outs.size();
   std::vector<int32_t> len(n_rows, 0);
   inc_ptr.assign(n_rows + 1, 0);
@@ -170,18 +170,23 @@ void pack_ell(const std::vector<SubOut>& outs, bool plus, const std::vector<int6
   E.width.assign(n_slices, 0);
   for (int64_t r = 0; r < n_rows; ++r)
     E.width[r / kSlice] = std::max(E.width[r / kSlice], len[r]);
-  E.col.assign(n_slices * kSlice * (int64_t)W, -1);
-  inc_tet.assign(inc_ptr[n_rows], 0);
-  inc_code.assign(inc_ptr[n_rows], 0);
+  // every entry is written exactly once below: the slots of each row by the thread of
+  // its subdomain (padding slots -1), the rows past n_rows in the last slice here
+  E.col.resize(n_slices * kSlice * (int64_t)W);
+  inc_tet.resize(inc_ptr[n_rows]);
+  inc_code.resize(inc_ptr[n_rows]);
+  for (int64_t row = n_rows; row < n_slices * kSlice; ++row)
+    for (int64_t j = 0; j < W; ++j)
+      E.col[(row / kSlice) * kSlice * W + j * kSlice + (row % kSlice)] = -1;
   parallel_for(n_sd, n_threads, [&](int i, int) {
     const LocalRows& R = plus ? outs[i].P : outs[i].W;
     const int64_t nr = (int64_t)R.ptr.size() - 1;
     for (int64_t r = 0; r < nr; ++r) {
       const int64_t row = off[i] + r, s = row / kSlice;
       const int64_t l = R.ptr[r + 1] - R.ptr[r];
-      for (int64_t j = 0; j < l; ++j)
+      for (int64_t j = 0; j < W; ++j)
         E.col[s * kSlice * W + j * kSlice + (row % kSlice)] =
-            (int32_t)(off[i] + R.cols[R.ptr[r] + j]);
+            j < l ? (int32_t)(off[i] + R.cols[R.ptr[r] + j]) : -1;
       int64_t q = inc_ptr[row];
       for (int64_t k = R.inc_ptr[r]; k < R.inc_ptr[r + 1]; ++k, ++q) {
         inc_tet[q] = R.inc_tet[k];
@@ -329,28 +334,45 @@ int build_global_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
   // interface entries: free u, v sharing an element, owner(u) < owner(v)
   struct Entry {
     int32_t i, j, u, v;
-    bool operator<(const Entry& o) const {
-      if (i != o.i) return i < o.i;
-      if (j != o.j) return j < o.j;
-      if (u != o.u) return u < o.u;
-      return v < o.v;
-    }
-    bool operator==(const Entry& o) const {
-      return i == o.i && j == o.j && u == o.u && v == o.v;
-    }
   };
+  // Each free node u lists its free neighbours v with owner(v) > owner(u) once, in
+  // ascending order (a few dozen candidates, deduplicated locally), in chunks of nodes
+  // on all cores; the chunks are concatenated in node order and a stable sort by
+  // subdomain pair then yields the entries ordered by (i, j, u, v).
+  const int64_t chunk = 1 << 16;
+  const int n_chunks = (int)((n_nodes + chunk - 1) / chunk);
+  std::vector<std::vector<Entry>> parts(n_chunks);
+  const int nthr_e = (int)std::min(32u, std::max(1u, std::thread::hardware_concurrency()));
+  parallel_for(n_chunks, nthr_e, [&](int c, int) {
+    std::vector<int32_t> nb;
+    auto& out = parts[c];
+    const int64_t u1 = std::min(n_nodes, (int64_t)(c + 1) * chunk);
+    for (int64_t u = (int64_t)c * chunk; u < u1; ++u) {
+      if (dirichlet[u]) continue;
+      nb.clear();
+      for (int64_t q = g.n2t_ptr[u]; q < g.n2t_ptr[u + 1]; ++q)
+        for (int b = 0; b < 4; ++b) {
+          int32_t v = tets[4 * (int64_t)g.n2t[q] + b];
+          if (!dirichlet[v] && owner[v] > owner[u]) nb.push_back(v);
+        }
+      std::sort(nb.begin(), nb.end());
+      nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+      for (int32_t v : nb) out.push_back(Entry{owner[u], owner[v], (int32_t)u, v});
+    }
+  });
   std::vector<Entry> ents;
-  for (int64_t u = 0; u < n_nodes; ++u) {
-    if (dirichlet[u]) continue;
-    for (int64_t q = g.n2t_ptr[u]; q < g.n2t_ptr[u + 1]; ++q)
-      for (int b = 0; b < 4; ++b) {
-        int32_t v = tets[4 * (int64_t)g.n2t[q] + b];
-        if (dirichlet[v] || owner[v] <= owner[u]) continue;
-        ents.push_back(Entry{owner[u], owner[v], (int32_t)u, v});
-      }
+  {
+    size_t n_ent = 0;
+    for (const auto& pt : parts) n_ent += pt.size();
+    ents.reserve(n_ent);
+    for (auto& pt : parts) {
+      ents.insert(ents.end(), pt.begin(), pt.end());
+      std::vector<Entry>().swap(pt);
+    }
   }
-  std::sort(ents.begin(), ents.end());
-  ents.erase(std::unique(ents.begin(), ents.end()), ents.end());
+  std::stable_sort(ents.begin(), ents.end(), [](const Entry& a, const Entry& b) {
+    return a.i != b.i ? a.i < b.i : a.j < b.j;
+  });
   g.pair_ptr.assign(1, 0);
   for (size_t q = 0; q < ents.size(); ++q) {
     if (q == 0 || ents[q].i != ents[q - 1].i || ents[q].j != ents[q - 1].j) {
@@ -390,9 +412,12 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
   int nthr = (int)std::max(1u, std::thread::hardware_concurrency());
   nthr = std::min({nthr, 32, std::max(1, (int)(24e9 / per_thread)), std::max(nw, 1)});
   auto& scratch = ps.impl->s;
-  while ((int)scratch.size() < nthr) {
-    scratch.emplace_back();
-    scratch.back().init(n_nodes, n_tets);
+  const int have = (int)scratch.size();
+  if (have < nthr) {
+    // zero the new scratch on the threads themselves (parallel first touch)
+    scratch.resize(nthr);
+    parallel_for(nthr - have, nthr - have,
+                 [&](int q, int) { scratch[have + q].init(n_nodes, n_tets); });
   }
   w.sets.resize(nw);
   std::vector<SubOut> outs(nw);

@@ -3,10 +3,37 @@
 // Pure C++; no CUDA types.
 #pragma once
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace mor {
+
+// Allocator whose resize() leaves new elements default-initialised (uninitialised for
+// integers): the large plan arrays are written in full by the threads that build them,
+// so no serial zero fill touches their pages first.
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using BigVec = std::vector<T, UninitAlloc<T>>;
 
 constexpr int kSlice = 32;      // sliced-ELL slice height (rows)
 constexpr int kTileRows = 128;  // rows per CUDA block tile in row-tiled kernels
@@ -18,7 +45,7 @@ struct HostEll {
   int64_t n_rows = 0;
   int32_t W = 0;
   std::vector<int32_t> width;  // per slice
-  std::vector<int32_t> col;
+  BigVec<int32_t> col;
 };
 
 // Row tiles of one row set; a tile never straddles two subdomains.
@@ -57,8 +84,8 @@ struct HostPlan {
   // code bits 0..1 = local vertex a of the row, bits 2+7b..8+7b = slot of vertex b
   // in the row's pattern (kNoSlot = not a DOF)
   std::vector<int64_t> incP_ptr, incW_ptr;
-  std::vector<int32_t> incP_tet, incW_tet;
-  std::vector<uint32_t> incP_code, incW_code;
+  BigVec<int32_t> incP_tet, incW_tet;
+  BigVec<uint32_t> incP_code, incW_code;
   HostTiles tP_all, tP_I, tP_B, tW, tO;
   // interface entries (u in sd i, v in sd j, i < j, u ~ v through an element)
   std::vector<int32_t> pair_i, pair_j;
