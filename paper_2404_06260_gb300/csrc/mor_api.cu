@@ -960,7 +960,7 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   launch_rowmul(S.tO, V, kq, mcols + 1, Mm, kq, Bo.Q, kq, mcols + 1, st);
   // b~_i = Q_i^T b[P_i]
   launch_gather_rows(nO, S.o2w, loadW, 1, 0, bP, 1, 0, 1, st);
-  launch_gram(S.tO, n_sd, Bo.Q, kq, kq, bP, 1, 1, gpart, gcnt, Bo.bt, kq, st);
+  launch_gram_vec(S.tO, n_sd, Bo.Q, kq, kq, bP, 1, gpart, gcnt, Bo.bt, kq, st);
   CK(cudaGetLastError());
 
   Bo.h_kept.resize(n_sd);

@@ -281,11 +281,21 @@ void launch_gram(const DTiles& tiles, int n_sd, const double* X, int ldx, int nx
   (void)n_sd;
   if (tiles.n <= 0) return;
   size_t sm = sizeof(double) * kGramRows * (nx + ny);
-  int sd_stride = (ny == 1) ? ldg : ldg * ldg;
-  int ldrow = (ny == 1) ? 1 : ldg;
   count_launch();
   k_gram<<<tiles.n, kGramThreads, sm, st>>>(tiles, X, ldx, nx, Y, ldy, ny, part, counter, G,
-                                           ldrow, sd_stride);
+                                           ldg, ldg * ldg);
+}
+
+void launch_gram_vec(const DTiles& tiles, int n_sd, const double* X, int ldx, int nx,
+                     const double* y, int ldy, double* part, int* counter, double* g, int ldg,
+                     cudaStream_t st) {
+  (void)n_sd;
+  if (tiles.n <= 0) return;
+  size_t sm = sizeof(double) * kGramRows * (nx + 1);
+  count_launch();
+  // the nx x 1 product, rows of stride 1 and ldg per subdomain
+  k_gram<<<tiles.n, kGramThreads, sm, st>>>(tiles, X, ldx, nx, y, ldy, 1, part, counter, g, 1,
+                                           ldg);
 }
 
 void launch_sym_eig(int n_sd, const double* A, int ld, int n, double* evals,

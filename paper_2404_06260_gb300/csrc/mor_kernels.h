@@ -207,11 +207,14 @@ void launch_cast(const DTiles& tiles, const double* src, T* dst, int kp, cudaStr
 
 // ---------------- dense per-subdomain kernels (mor_dense.cu) ----------------
 // G[sd] = X^T Y over the rows of tiles: nx x ny with row stride ldg and subdomain
-// stride ldg*ldg, or for ny == 1 a vector with subdomain stride ldg.
-// part: n_tiles x nx x ny doubles.
+// stride ldg*ldg (also for nx = ny = 1).  part: n_tiles x nx x ny doubles.
 void launch_gram(const DTiles& tiles, int n_sd, const double* X, int ldx, int nx,
                  const double* Y, int ldy, int ny, double* part, int* counter, double* G,
                  int ldg, cudaStream_t st);
+// x_sd^T y per subdomain for one column y: g[sd * ldg + i] (ldg >= nx)
+void launch_gram_vec(const DTiles& tiles, int n_sd, const double* X, int ldx, int nx,
+                     const double* y, int ldy, double* part, int* counter, double* g,
+                     int ldg, cudaStream_t st);
 // symmetric eigensolver (cyclic Jacobi, parallel ordering) per subdomain on the
 // leading n x n block of A[sd] (stride ld); evals descending (n_sd x ld), evecs
 // columns (n_sd x ld x ld).

@@ -471,6 +471,14 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
       }
     std::sort(ss.I.begin(), ss.I.end());
     std::sort(ss.B.begin(), ss.B.end());
+    // a subdomain whose extension covers the whole domain has no lifting problem
+    // (Eq. (8) has no boundary data) and no interface; the batched kernels assume
+    // every subdomain has rows in I and in B
+    if (ss.B.empty() || ss.I.empty())
+      so.err = "subdomain " + std::to_string(i) +
+               (ss.B.empty() ? " has an empty boundary set B (its extension covers the "
+                               "domain: use more subdomains or fewer hops)"
+                             : " has an empty interior set I");
     // omega_i = elements touching P_i, ascending
     for (int32_t v : g.Pown[i])
       for (int64_t q = n2t_ptr[v]; q < n2t_ptr[v + 1]; ++q) {

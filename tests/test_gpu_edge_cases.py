@@ -1,0 +1,99 @@
+"""Degenerate cases of the method on the GPU path, against the oracle (binary64 path, the
+16^3 cube with its lognormal coefficient).
+
+- The smallest sketch, k = 1 (rank 1, no oversampling): one Gaussian column per
+  subdomain, so sigma_1 is a single randomized sample; it and the reduced energy match
+  the oracle's (the same Philox draws).  Columns 1..3 of every 4-wide block are padding.
+- Tolerance mode at its extremes (Eq. (15)): eps above every sigma keeps only the load
+  column u_0 of each subdomain; eps far below keeps every sketched direction.
+- The smallest partition, two subdomains sharing one interface.
+
+Tolerances as in the 16^3 parity tests: sigma to 1e-10 sigma_1, reduced energy and the
+lifted solution to 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pipeline, reduced
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mor():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2404_06260_gb300 import _build
+    _build.build()
+    from paper_2404_06260_gb300 import mor as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def cube16():
+    return synth.workload("cube16_p2")
+
+
+def _gpu(mor, mesh, kappa, owner, r_hops, rank, oversample, seed, eps=0.0):
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, r_hops)
+    b = mor.Bases(sd, mor.basis_opts(rank=rank, oversample=oversample, seed=seed,
+                                     precision="fp64", cg_rtol=1e-13, eps=eps))
+    assert b.converged
+    r = mor.Reduced(sd, b)
+    x, info = r.solve(rtol=1e-14)
+    assert info["converged"]
+    return b, info, mor.lift(sd, b, x).cpu().numpy()
+
+
+def _same_solution(mesh, kappa, ref, info, u):
+    assert abs(info["energy"] - ref["E"]) <= 1e-10 * ref["E"]
+    assert reduced.energy_norm(mesh, kappa, u - ref["u_red"]) <= \
+        1e-10 * reduced.energy_norm(mesh, kappa, ref["u_red"])
+
+
+def test_smallest_sketch_one_column(mor, cube16):
+    mesh, kappa, owner, p = cube16
+    ref = pipeline.run(mesh, kappa, owner, 1, 0, p["r_hops"], p["seed"], fe_solution=False)
+    b, info, u = _gpu(mor, mesh, kappa, owner, p["r_hops"], 1, 0, p["seed"])
+    sg = b.sigma()
+    for i, ob in enumerate(ref["bases"]):
+        assert abs(sg[i, 0] - ob["sigma"][0]) <= 1e-10 * ob["sigma"][0]
+        assert b.kept[i] == ob["n_kept"] == 2          # u_0 and the one direction
+    _same_solution(mesh, kappa, ref, info, u)
+
+
+@pytest.mark.parametrize("which", ["above_all", "below_all"])
+def test_tolerance_mode_extremes(mor, cube16, which):
+    mesh, kappa, owner, p = cube16
+    k = p["rank"] + p["oversample"]
+    ref0 = pipeline.run(mesh, kappa, owner, p["rank"], p["oversample"], p["r_hops"],
+                        p["seed"], fe_solution=False)
+    sig = np.concatenate([ob["sigma"][:k] for ob in ref0["bases"]])
+    assert sig.min() > 1e-8
+    eps = 10.0 * sig.max() if which == "above_all" else 1e-12
+    ref = pipeline.run(mesh, kappa, owner, p["rank"], p["oversample"], p["r_hops"],
+                       p["seed"], eps=eps, fe_solution=False)
+    b, info, u = _gpu(mor, mesh, kappa, owner, p["r_hops"], p["rank"], p["oversample"],
+                      p["seed"], eps=eps)
+    m_or = np.array([ob["m"] for ob in ref["bases"]])
+    assert np.all(m_or == (0 if which == "above_all" else k))
+    assert np.array_equal(b.kept, [ob["n_kept"] for ob in ref["bases"]])
+    if which == "above_all":
+        assert np.all(b.kept == 1)                     # u_0 alone
+    _same_solution(mesh, kappa, ref, info, u)
+
+
+def test_two_subdomains(mor, cube16):
+    mesh, kappa, owner, p = cube16
+    two = (mesh.xyz[:, 0] > 0.5).astype(owner.dtype)
+    ref = pipeline.run(mesh, kappa, two, p["rank"], p["oversample"], p["r_hops"], p["seed"],
+                       fe_solution=False)
+    b, info, u = _gpu(mor, mesh, kappa, two, p["r_hops"], p["rank"], p["oversample"],
+                      p["seed"])
+    sg = b.sigma()
+    k = p["rank"] + p["oversample"]
+    for i, ob in enumerate(ref["bases"]):
+        assert np.max(np.abs(sg[i, :k] - ob["sigma"][:k])) <= 1e-10 * ob["sigma"][0]
+    _same_solution(mesh, kappa, ref, info, u)

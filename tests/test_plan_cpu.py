@@ -52,3 +52,15 @@ def test_bad_partition_is_an_error_not_a_crash(mor):
     bad[bad == 3] = 9                       # label 3 unused
     with pytest.raises(mor.MorError):
         mor.plan_check(mesh, bad, p["r_hops"], 4)
+
+
+def test_single_subdomain_is_rejected_with_a_clear_error(mor):
+    # one subdomain: its extension is the whole domain, B is empty and Eq. (8) has no
+    # boundary data; the library refuses the plan instead of building empty batches
+    mesh, kappa, owner, p = synth.workload("cube16_p2")
+    with pytest.raises(mor.MorError, match="empty boundary set B"):
+        mor.plan_check(mesh, np.zeros_like(owner), p["r_hops"], 1)
+    # two subdomains are the smallest valid partition
+    two = (mesh.xyz[:, 0] > 0.5).astype(owner.dtype)
+    c = mor.plan_check(mesh, two, p["r_hops"], 2)
+    assert c["n_sub"] == 2 and c["wave_mismatches"] == 0
