@@ -7,6 +7,10 @@
 - Tolerance mode at its extremes (Eq. (15)): eps above every sigma keeps only the load
   column u_0 of each subdomain; eps far below keeps every sketched direction.
 - The smallest partition, two subdomains sharing one interface.
+- The widest sketch the kernels take, k = 79 (kp = 80 columns, the limit of the
+  shared-memory eigensolver and of the CG blocks), and the error beyond it.
+- The mixed path at k = 1 (three of the four binary32 columns of a pack are padding)
+  and at k = 79, within 1e-6 in energy of the binary64 path.
 
 Tolerances as in the 16^3 parity tests: sigma to 1e-10 sigma_1, reduced energy and the
 lifted solution to 1e-10 relative.
@@ -35,11 +39,13 @@ def cube16():
     return synth.workload("cube16_p2")
 
 
-def _gpu(mor, mesh, kappa, owner, r_hops, rank, oversample, seed, eps=0.0):
+def _gpu(mor, mesh, kappa, owner, r_hops, rank, oversample, seed, eps=0.0,
+         precision="fp64"):
     gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
     sd = mor.Subdomains(gm, owner, r_hops)
+    rtol = 1e-13 if precision == "fp64" else 1e-9
     b = mor.Bases(sd, mor.basis_opts(rank=rank, oversample=oversample, seed=seed,
-                                     precision="fp64", cg_rtol=1e-13, eps=eps))
+                                     precision=precision, cg_rtol=rtol, eps=eps))
     assert b.converged
     r = mor.Reduced(sd, b)
     x, info = r.solve(rtol=1e-14)
@@ -62,6 +68,15 @@ def test_smallest_sketch_one_column(mor, cube16):
         assert abs(sg[i, 0] - ob["sigma"][0]) <= 1e-10 * ob["sigma"][0]
         assert b.kept[i] == ob["n_kept"] == 2          # u_0 and the one direction
     _same_solution(mesh, kappa, ref, info, u)
+    _mixed_close(mor, mesh, kappa, owner, p, 1, 0, b, u)
+
+
+def _mixed_close(mor, mesh, kappa, owner, p, rank, oversample, b64, u64):
+    bm, _, um = _gpu(mor, mesh, kappa, owner, p["r_hops"], rank, oversample, p["seed"],
+                     precision="mixed")
+    assert np.array_equal(bm.kept, b64.kept)
+    assert reduced.energy_norm(mesh, kappa, um - u64) <= \
+        1e-6 * reduced.energy_norm(mesh, kappa, u64)
 
 
 @pytest.mark.parametrize("which", ["above_all", "below_all"])
@@ -97,3 +112,26 @@ def test_two_subdomains(mor, cube16):
     for i, ob in enumerate(ref["bases"]):
         assert np.max(np.abs(sg[i, :k] - ob["sigma"][:k])) <= 1e-10 * ob["sigma"][0]
     _same_solution(mesh, kappa, ref, info, u)
+
+
+def test_widest_sketch_79_columns(mor, cube16):
+    mesh, kappa, owner, p = cube16
+    rank, over = 69, 10
+    ref = pipeline.run(mesh, kappa, owner, rank, over, p["r_hops"], p["seed"],
+                       fe_solution=False)
+    b, info, u = _gpu(mor, mesh, kappa, owner, p["r_hops"], rank, over, p["seed"])
+    sg = b.sigma()
+    assert sg.shape[1] == 79
+    for i, ob in enumerate(ref["bases"]):
+        assert np.max(np.abs(sg[i] - ob["sigma"][:79])) <= 1e-10 * ob["sigma"][0]
+    assert np.array_equal(b.kept, [ob["n_kept"] for ob in ref["bases"]])
+    _same_solution(mesh, kappa, ref, info, u)
+    _mixed_close(mor, mesh, kappa, owner, p, rank, over, b, u)
+
+
+def test_sketch_wider_than_79_is_an_error(mor, cube16):
+    mesh, kappa, owner, p = cube16
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, p["r_hops"])
+    with pytest.raises(mor.MorError, match="<= 79"):
+        mor.Bases(sd, mor.basis_opts(rank=70, oversample=10, seed=p["seed"]))
