@@ -61,6 +61,21 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(t_ms, cols, world, device):
+    """Whole-job figures of the replicas: the slowest rank's time and the basis columns
+    of all ranks (value = columns / that time).  One process per GPU; `device` is the
+    tensor device of the process group's backend."""
+    if world == 1:
+        return float(t_ms), float(cols)
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    tot = torch.tensor([float(cols)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tot[0])
+
+
 class Clocks:
     """nvidia-smi samples during the timed region (every 200 ms)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -250,14 +265,7 @@ def ours(args):
     if world > 1:
         dist.barrier()
     t_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    t_max = t_ms
-    tot_cols = cols
-    if world > 1:
-        tt = torch.tensor([t_ms, float(cols)], dtype=torch.float64, device="cuda")
-        tmax = tt.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max, tot_cols = float(tmax[0]), float(tt[1])
+    t_max, tot_cols = reduce_over_ranks(t_ms, cols, world, "cuda")
     value = tot_cols / (t_max / 1e3)
 
     # dominant kernel of the timed region and its roofline
@@ -299,7 +307,7 @@ def ours(args):
     # end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(args, mor, mesh, kappa, owner, p, mixed, b, stream, world)
+        e2e = end_to_end(args, mor, mesh, kappa, owner, p, mixed, stream, world)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -331,7 +339,7 @@ def ours(args):
     return 0
 
 
-def end_to_end(args, mor, mesh, kappa, owner, p, mixed, b, stream, world):
+def end_to_end(args, mor, mesh, kappa, owner, p, mixed, stream, world):
     """The same metric through the public API with the mesh in pinned host memory: every
     step copies it to the device, runs steps 1-3 and reads x back."""
     import torch
@@ -340,7 +348,7 @@ def end_to_end(args, mor, mesh, kappa, owner, p, mixed, b, stream, world):
     kap_h = torch.from_numpy(kappa).pin_memory()
     h2d = (xyz_h.numel() * 8 + tets_h.numel() * 4 * 2 + kap_h.numel() * 8 +
            mesh.dirichlet.nbytes + owner.nbytes)
-    e2e_ms, d2h = [], 0
+    e2e_ms, d2h, cols = [], 0, 0
     for i in range(args.steps):
         torch.cuda.synchronize()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -358,10 +366,11 @@ def end_to_end(args, mor, mesh, kappa, owner, p, mixed, b, stream, world):
         torch.cuda.synchronize()
         e2e_ms.append(s0.elapsed_time(s1))
         d2h = xh.numel() * 8
+        cols += b2.total_kept
         del sd2, b2, r2
-    e2e_val = b.total_kept / (statistics.mean(e2e_ms) / 1e3) * world
-    return {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)}
+    t_max, tot_cols = reduce_over_ranks(sum(e2e_ms), cols, world, "cuda")
+    return {"value": tot_cols / (t_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": t_max / args.steps}
 
 
 def profile_case(args):
