@@ -61,6 +61,25 @@ def dist_env():
     return rank, world, local
 
 
+def rank_opts(p):
+    """Sketch widths of a workload: one rank for all subdomains, or seeded
+    per-subdomain ranks (uneven batches)."""
+    kw = dict(rank=p["rank"], oversample=p["oversample"], seed=p["seed"])
+    if "ranks" in p:
+        kw["ranks"] = p["ranks"]
+    return kw
+
+
+def mixed_rtol(p):
+    """Local-solve tolerance of the mixed path: 1e-9, or tighter where the coefficient
+    contrast makes the energy error of a solve larger (about rtol sqrt(cond A_II))."""
+    return p.get("mixed_rtol", 1e-9)
+
+
+def first_rank(p):
+    return int(p["ranks"][0]) if "ranks" in p else p["rank"]
+
+
 def reduce_over_ranks(t_ms, cols, world, device):
     """Whole-job figures of the replicas: the slowest rank's time and the basis columns
     of all ranks (value = columns / that time).  One process per GPU; `device` is the
@@ -161,7 +180,7 @@ def reference_arm(args):
     s = subdomains.subdomain_sets(mesh, owner, sub, p["r_hops"], adj)
 
     def step():
-        b = basis.local_basis(mesh, kappa, s, p["rank"], p["oversample"], p["seed"])
+        b = basis.local_basis(mesh, kappa, s, first_rank(p), p["oversample"], p["seed"])
         return b["n_kept"]
 
     for _ in range(args.warmup):
@@ -182,7 +201,7 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "subdomains": 1, "rank": p["rank"],
+        "config": {"workload": args.workload, "subdomains": 1, "rank": first_rank(p),
                    "oversample": p["oversample"]},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -198,7 +217,7 @@ def cpu_baseline(args):
     adj = subdomains.node_adjacency(mesh.tets, mesh.n_nodes)
     s = subdomains.subdomain_sets(mesh, owner, 0, p["r_hops"], adj)
     t0 = time.perf_counter()
-    b = basis.local_basis(mesh, kappa, s, p["rank"], p["oversample"], p["seed"])
+    b = basis.local_basis(mesh, kappa, s, first_rank(p), p["oversample"], p["seed"])
     dt = time.perf_counter() - t0
     return {"value": b["n_kept"] / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": "oracle local basis (field sketch, FP64, sparse LU + dense LAPACK) of "
@@ -227,10 +246,9 @@ def ours(args):
     gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
     sd = mor.Subdomains(gm, owner, p["r_hops"], wave=args.wave)
     a1_ms = 1e3 * (time.perf_counter() - t0)
-    mixed = mor.basis_opts(rank=p["rank"], oversample=p["oversample"], seed=p["seed"],
-                           precision="mixed", cg_rtol=1e-9)
-    fp64 = mor.basis_opts(rank=p["rank"], oversample=p["oversample"], seed=p["seed"],
-                          precision="fp64", cg_rtol=1e-10)
+    mixed = mor.basis_opts(precision="mixed", cg_rtol=mixed_rtol(p), **rank_opts(p))
+    fp64 = mor.basis_opts(precision="fp64", cg_rtol=min(1e-10, mixed_rtol(p)),
+                          **rank_opts(p))
 
     def step(opts):
         b = mor.Bases(sd, opts)
@@ -315,11 +333,14 @@ def ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": args.workload, "mesh": "%d^3 cells x 6 Kuhn tets" % p["n"],
-                   "subdomains": sd.n_sub, "rank": p["rank"], "oversample": p["oversample"],
+                   "subdomains": sd.n_sub,
+                   "rank": ("per subdomain, %d..%d" % p["rank_range"]) if "ranks" in p
+                   else p["rank"], "oversample": p["oversample"],
                    "r_hops": p["r_hops"], "precision": "mixed (f32 CG sweeps, f64 refinement "
                    "and small dense work)", "parallelism": "replicas x%d" % world,
                    "l2": "working set > L2 and a 256 MB L2 flush between steps",
-                   "basis_cols_per_step": int(b.total_kept)},
+                   "basis_cols_per_step": int(b.total_kept),
+                   "cg_rtol": {"mixed": mixed_rtol(p), "fp64": min(1e-10, mixed_rtol(p))}},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -383,8 +404,7 @@ def profile_case(args):
     mesh, kappa, owner, p = synth.workload(args.workload)
     gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
     sd = mor.Subdomains(gm, owner, p["r_hops"])
-    opts = mor.basis_opts(rank=p["rank"], oversample=p["oversample"], seed=p["seed"],
-                          precision="mixed", cg_rtol=1e-9)
+    opts = mor.basis_opts(precision="mixed", cg_rtol=mixed_rtol(p), **rank_opts(p))
     b = mor.Bases(sd, opts)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.workload, "basis_cols": int(b.total_kept),
