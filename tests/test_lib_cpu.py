@@ -38,3 +38,20 @@ def test_error_message_without_gpu_work():
     assert o.rank == 12 and o.oversample == 3 and o.precision == mor.MIXED
     rc = mor._lib.mor_build_bases(None, ctypes.byref(o), None, None)
     assert rc == -1 and b"null" in mor._lib.mor_last_error()
+
+
+def test_binding_fails_loudly_without_the_library():
+    # no fallback: with libmor.so absent, importing the binding raises ImportError
+    import subprocess
+    import sys
+    code = ("import os, sys; sys.path.insert(0, %r); real = os.path.exists; "
+            "os.path.exists = lambda p: False if str(p).endswith('libmor.so') else real(p)\n"
+            "try:\n"
+            "    import paper_2404_06260_gb300.mor\n"
+            "except ImportError as e:\n"
+            "    print('ImportError', e)\n"
+            "else:\n"
+            "    print('imported')\n") % ROOT
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT)
+    assert out.stdout.startswith("ImportError") and "not built" in out.stdout, out

@@ -64,3 +64,27 @@ def test_single_subdomain_is_rejected_with_a_clear_error(mor):
     two = (mesh.xyz[:, 0] > 0.5).astype(owner.dtype)
     c = mor.plan_check(mesh, two, p["r_hops"], 2)
     assert c["n_sub"] == 2 and c["wave_mismatches"] == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_partitions_match_the_oracle(mor, seed):
+    # seeded k-means partitions of a jittered 10^3 cube, random hops and wave size:
+    # either every invariant holds, or (an extension covering the domain) the plan is
+    # rejected exactly when the oracle finds a subdomain with an empty B
+    rng = np.random.default_rng(100 + seed)
+    mesh = synth.kuhn_cube(10, jitter=0.2, seed=200 + seed)
+    parts = int(rng.integers(3, 9))
+    owner = synth.kmeans_owner(mesh, parts, 300 + seed)
+    r_hops = int(rng.integers(1, 5))
+    n_sub = int(owner.max()) + 1
+    wave = int(rng.integers(1, n_sub + 1))
+    subs = osub.all_subdomains(mesh, owner, r_hops)
+    if any(len(s["B"]) == 0 for s in subs):
+        with pytest.raises(mor.MorError, match="empty boundary set B"):
+            mor.plan_check(mesh, owner, r_hops, wave)
+        return
+    c = mor.plan_check(mesh, owner, r_hops, wave)
+    assert c["n_sub"] == n_sub and c["wave_mismatches"] == 0
+    assert c["aggregate_violations"] == 0
+    assert c["owned"] == sum(len(s["owned"]) for s in subs)
+    assert c["rows"] == sum(len(s["I"]) + len(s["B"]) for s in subs)
