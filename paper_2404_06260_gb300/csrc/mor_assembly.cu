@@ -122,16 +122,20 @@ __global__ void k_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* __rest
                              const float2* __restrict__ lsplit, int k, uint64_t seed,
                              uint32_t sd_base, double* __restrict__ out, int ld,
                              const int32_t* __restrict__ k_sd) {
-  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= n_rows) return;
+  // one thread per (row, column): consecutive threads take consecutive columns of a
+  // row (coalesced stores; the threads of a row read the same incidence entries)
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n_rows * (int64_t)k) return;
+  const int64_t w = idx / k;
+  const int j = (int)(idx - w * k);
   int64_t r = row0 + w;
   uint32_t sd = (uint32_t)row_sd[r];
   const uint32_t sd_id = sd + sd_base;  // the subdomain's id in the whole batch
   int64_t q0 = inc_ptr[r], q1 = inc_ptr[r + 1];
   const int kk = k_sd ? min(k, (int)k_sd[sd]) : k;
-  for (int j = lane + kk; j < k; j += 32) out[r * ld + j] = 0.0;
-  for (int j = lane; j < kk; j += 32) {
+  if (j >= kk) {
+    out[r * ld + j] = 0.0;
+  } else {
     float hi = 0.f, lo = 0.f;
     for (int64_t q = q0; q < q1; ++q) {
       float z[4];
@@ -158,7 +162,7 @@ void launch_sketch_rhs(int64_t row0, int64_t n_rows, const int32_t* row_sd,
                        const int32_t* k_sd) {
   if (n_rows <= 0) return;
   int bs = 256;
-  unsigned grid = (unsigned)((n_rows * 32 + bs - 1) / bs);
+  unsigned grid = (unsigned)((n_rows * (int64_t)k + bs - 1) / bs);
   count_launch();
   k_sketch_rhs<<<grid, bs, 0, st>>>(row0, n_rows, row_sd, inc_ptr, inc_tet, inc_code, lsplit,
                                     k, seed, sd_base, out, ld, k_sd);
