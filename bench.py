@@ -14,7 +14,8 @@ e2e    = the same metric through the public Python API from host buffers: pinned
          host -> device copy of the mesh, step 1 on the host, steps 2-3, and the
          device -> host read of the reduced solution, every step.
 --impl reference runs the CPU oracle (test infrastructure, plain FP64 NumPy/SciPy) on
-a bounded sample of the same workload: one subdomain's local basis per step.
+the host cores, one single-threaded process per core, on a bounded sample of the same
+workload: the local bases of the `cores` smallest subdomains per step.
 """
 from __future__ import annotations
 
@@ -48,6 +49,9 @@ def parse():
                          "subdomains (the 440^3 workload)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--explicit-vs-randomized", action="store_true",
+                    help="time the explicit weighted SVD (Eq. (14), dense factors) against "
+                         "the randomized one on the 16^3 workload and exit (Sec. 7.2)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run one mixed-precision build of the workload and exit (the "
                          "command profiled by ncu)")
@@ -167,63 +171,134 @@ def ncu_traffic(kernel_key):
     return entry.get("dram_bytes_per_launch_scaled")
 
 
+_ORACLE_CACHE = {}
+
+
+def _oracle_subdomain(task):
+    """One subdomain's local basis by the oracle (a process-pool task): returns
+    (subdomain, basis columns, seconds)."""
+    workload, sub = task
+    import synth
+    from oracle import basis, subdomains
+    if workload not in _ORACLE_CACHE:
+        mesh, kappa, owner, p = synth.workload(workload)
+        adj = subdomains.node_adjacency(mesh.tets, mesh.n_nodes)
+        _ORACLE_CACHE.clear()
+        _ORACLE_CACHE[workload] = (mesh, kappa, owner, p, adj)
+    mesh, kappa, owner, p, adj = _ORACLE_CACHE[workload]
+    t0 = time.perf_counter()
+    s = subdomains.subdomain_sets(mesh, owner, sub, p["r_hops"], adj)
+    m = int(p["ranks"][sub]) if "ranks" in p else p["rank"]
+    b = basis.local_basis(mesh, kappa, s, m, p["oversample"], p["seed"])
+    return sub, int(b["n_kept"]), time.perf_counter() - t0
+
+
+def oracle_pool(cores):
+    """A pool of `cores` single-threaded oracle processes.  Started with spawn, so that no
+    worker is forked from a process holding a CUDA context; each worker runs one BLAS
+    thread, so the pool uses exactly `cores` threads."""
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    return mp.get_context("spawn").Pool(processes=cores)
+
+
+def oracle_extension_sizes(workload):
+    """|I| + |B| of every subdomain of a workload (the oracle's own sets)."""
+    import numpy as np
+    import synth
+    from oracle import subdomains
+    mesh, kappa, owner, p = synth.workload(workload)
+    adj = subdomains.node_adjacency(mesh.tets, mesh.n_nodes)
+    n_sub = int(owner.max()) + 1
+    out = np.zeros(n_sub, dtype=np.int64)
+    for i in range(n_sub):
+        s = subdomains.subdomain_sets(mesh, owner, i, p["r_hops"], adj)
+        out[i] = len(s["I"]) + len(s["B"])
+    return out
+
+
 def reference_arm(args):
+    """The oracle on the host cores: every step runs the local bases of the `cores`
+    subdomains with the smallest extensions, one per single-threaded process, and the
+    metric is their basis columns over the step's wall time.  The smallest subdomains
+    keep a step near one subdomain's oracle time (the run must end within minutes), so
+    the rate over-states the oracle's rate on the whole batch, whose larger subdomains
+    take up to about 3x longer."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import numpy as np  # noqa: F401
+    import numpy as np
     import synth
-    from oracle import basis, subdomains
-    mesh, kappa, owner, p = synth.workload(args.workload)
-    adj = subdomains.node_adjacency(mesh.tets, mesh.n_nodes)
-    sub = 0   # the smallest (corner) subdomain: an upper bound on the oracle's rate
-    s = subdomains.subdomain_sets(mesh, owner, sub, p["r_hops"], adj)
-
-    def step():
-        b = basis.local_basis(mesh, kappa, s, first_rank(p), p["oversample"], p["seed"])
-        return b["n_kept"]
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    cols = 0
-    for _ in range(args.steps):
-        cols += step()
-    dt = time.perf_counter() - t0
+    p = synth.workload(args.workload)[3]
+    cores = os.cpu_count() or 1
+    sizes = oracle_extension_sizes(args.workload)
+    sample = [int(i) for i in np.argsort(sizes, kind="stable")[:cores]]
+    pool = oracle_pool(len(sample))
+    try:
+        tasks = [(args.workload, i) for i in sample]
+        pool.map(_oracle_subdomain, tasks[:1])   # worker start-up (untimed)
+        for _ in range(args.warmup):
+            pool.map(_oracle_subdomain, tasks)
+        t0 = time.perf_counter()
+        cols = 0
+        for _ in range(args.steps):
+            cols += sum(c for _, c, _ in pool.map(_oracle_subdomain, tasks))
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
     val = cols / dt
-    cores = os.cpu_count()
-    sample = ("oracle local basis of subdomain %d of %s (|I|=%d, |B|=%d), %d steps; the "
-              "corner subdomain is the cheapest, so this is an upper bound on the oracle's "
-              "rate over the whole batch" % (sub, args.workload, len(s["I"]), len(s["B"]),
-                                             args.steps))
+    desc = ("oracle local bases (field sketch, FP64, SuperLU + LAPACK) of the %d subdomains "
+            "of %s with the smallest extensions (|I|+|B| %d..%d of %d..%d over the batch), "
+            "one per single-threaded process on %d host cores, %d steps; an upper bound "
+            "on the oracle's rate over the whole batch"
+            % (len(sample), args.workload, sizes[sample].min(), sizes[sample].max(),
+               sizes.min(), sizes.max(), len(sample), args.steps))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "subdomains": 1, "rank": first_rank(p),
-                   "oversample": p["oversample"]},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+        "config": {"workload": args.workload, "subdomains": len(sample),
+                   "rank": first_rank(p), "oversample": p["oversample"]},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": len(sample), "kind": "oracle",
+                         "sample": desc},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
     return 0
 
 
 def cpu_baseline(args):
+    """The oracle over the host cores on a seeded random sample of the batch: one
+    subdomain per single-threaded process, `cores` subdomains, one round."""
+    import numpy as np
     import synth
-    from oracle import basis, subdomains
+    cores = os.cpu_count() or 1
     mesh, kappa, owner, p = synth.workload(args.workload)
-    adj = subdomains.node_adjacency(mesh.tets, mesh.n_nodes)
-    s = subdomains.subdomain_sets(mesh, owner, 0, p["r_hops"], adj)
-    t0 = time.perf_counter()
-    b = basis.local_basis(mesh, kappa, s, first_rank(p), p["oversample"], p["seed"])
-    dt = time.perf_counter() - t0
-    return {"value": b["n_kept"] / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle local basis (field sketch, FP64, sparse LU + dense LAPACK) of "
-                      "subdomain 0 of %s, the smallest (corner) subdomain: %.1f s for %d "
-                      "columns; an upper bound on the oracle's rate over the batch"
-                      % (args.workload, dt, b["n_kept"])}
+    n_sub = int(owner.max()) + 1
+    rng = np.random.default_rng(12345)
+    sample = sorted(int(i) for i in rng.choice(n_sub, size=min(cores, n_sub), replace=False))
+    pool = oracle_pool(len(sample))
+    try:
+        pool.map(_oracle_subdomain, [(args.workload, sample[0])])   # start-up (untimed)
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_subdomain, [(args.workload, i) for i in sample])
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    cols = sum(c for _, c, _ in res)
+    per = [t for _, _, t in res]
+    return {"value": cols / dt, "unit": UNIT, "cores": len(sample), "kind": "oracle",
+            "sample": "oracle local bases (field sketch, FP64, SuperLU + LAPACK) of %d "
+                      "subdomains of %s drawn at random (seed 12345) from all %d, one per "
+                      "single-threaded process on %d host cores: %.1f s wall for %d "
+                      "columns; per subdomain %.1f..%.1f s (mean %.1f), so the whole "
+                      "batch would take about %.0f s on these cores (extrapolated)"
+                      % (len(sample), args.workload, n_sub, len(sample), dt, cols,
+                         min(per), max(per), float(np.mean(per)),
+                         float(np.mean(per)) * n_sub / len(sample))}
 
 
 def ours(args):
@@ -362,23 +437,22 @@ def ours(args):
 
 def end_to_end(args, mor, mesh, kappa, owner, p, mixed, stream, world):
     """The same metric through the public API with the mesh in pinned host memory: every
-    step copies it to the device, runs steps 1-3 and reads x back."""
+    step hands the host arrays to step 1 (mor_build_subdomains_host copies them to the
+    device inside the call while it builds the plan on the host), runs steps 2-3 and
+    reads x back."""
     import torch
     xyz_h = torch.from_numpy(mesh.xyz).pin_memory()
     tets_h = torch.from_numpy(mesh.tets).pin_memory()
     kap_h = torch.from_numpy(kappa).pin_memory()
-    h2d = (xyz_h.numel() * 8 + tets_h.numel() * 4 * 2 + kap_h.numel() * 8 +
-           mesh.dirichlet.nbytes + owner.nbytes)
+    dir_h = torch.from_numpy(mesh.dirichlet).pin_memory()
+    h2d = xyz_h.numel() * 8 + tets_h.numel() * 4 + kap_h.numel() * 8
     e2e_ms, d2h, cols = [], 0, 0
     for i in range(args.steps):
         torch.cuda.synchronize()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        gm2 = mor.Mesh.from_device(xyz_h.to("cuda", non_blocking=True),
-                                   tets_h.to("cuda", non_blocking=True),
-                                   kap_h.to("cuda", non_blocking=True),
-                                   tets_h.numpy(), mesh.dirichlet)
-        sd2 = mor.Subdomains(gm2, owner, p["r_hops"], wave=args.wave)
+        sd2 = mor.Subdomains.from_host(xyz_h, tets_h, kap_h, dir_h, owner, p["r_hops"],
+                                       wave=args.wave)
         b2 = mor.Bases(sd2, mixed)
         r2 = mor.Reduced(sd2, b2)
         x2, _ = r2.solve(rtol=1e-10)
@@ -391,7 +465,9 @@ def end_to_end(args, mor, mesh, kappa, owner, p, mixed, stream, world):
         del sd2, b2, r2
     t_max, tot_cols = reduce_over_ranks(sum(e2e_ms), cols, world, "cuda")
     return {"value": tot_cols / (t_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": t_max / args.steps}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": t_max / args.steps,
+            "inputs": "coordinates, connectivity and coefficient copied by the library "
+                      "(mor_build_subdomains_host); step 1 reads the host arrays"}
 
 
 def profile_case(args):
@@ -412,8 +488,57 @@ def profile_case(args):
     return 0
 
 
+def explicit_vs_randomized(args):
+    """Step 2 (mor_build_bases, binary64) on the 16^3 workload three ways: the field
+    sketch with k = m + p columns, the paper's sketch W = R_BB^{-1} S (dense Cholesky
+    of H^+), and the explicit weighted SVD of R_i Z_i R_BB^{-1} (dense factors of
+    A_II, H_i, H^+).  CUDA-event times, median of 5 after 2 warm-up builds."""
+    import torch
+
+    import synth
+    from paper_2404_06260_gb300 import _build
+    _build.build()
+    from paper_2404_06260_gb300 import mor
+    mesh, kappa, owner, p = synth.workload("cube16_p2")
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, p["r_hops"])
+    stream = torch.cuda.current_stream()
+    variants = {
+        "randomized_field": mor.basis_opts(rank=p["rank"], oversample=p["oversample"],
+                                           seed=p["seed"], precision="fp64", cg_rtol=1e-13),
+        "randomized_paper_sketch": mor.basis_opts(rank=p["rank"], oversample=p["oversample"],
+                                                  seed=p["seed"], precision="fp64",
+                                                  cg_rtol=1e-13, sketch="paper"),
+        "explicit": mor.basis_opts(rank=p["rank"], oversample=0, seed=p["seed"],
+                                   precision="fp64", explicit_svd=1),
+    }
+    out = {}
+    for name, o in variants.items():
+        for _ in range(2):
+            mor.Bases(sd, o)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            b = mor.Bases(sd, o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[name] = {"ms": statistics.median(ts), "basis_cols": int(b.total_kept),
+                     "sigma_1": float(b.sigma()[:, 0].max())}
+    print(json.dumps({"workload": "cube16_p2", "n_sub": sd.n_sub, "rank": p["rank"],
+                      "B_sizes": [int(sd.counts[:, 1].min()), int(sd.counts[:, 1].max())],
+                      "builds": out,
+                      "explicit_over_randomized": out["explicit"]["ms"] /
+                      out["randomized_field"]["ms"]}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.explicit_vs_randomized:
+        return explicit_vs_randomized(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.profile_case:

@@ -45,6 +45,8 @@ extern "C" {
 #define MOR_ERR_BAD_MESH (-2)       /* element with non-positive volume, bad index     */
 #define MOR_ERR_OOM (-3)            /* device or host allocation failed                */
 #define MOR_ERR_NOT_CONVERGED (-4)  /* an iterative solve hit max_iter (results kept)  */
+#define MOR_ERR_TIMEOUT (-5)        /* a bounded device-side wait ran out (the kernel
+                                       returned; the CUDA context stays usable)       */
 #define MOR_ERR_CUDA (-6)           /* CUDA runtime or launch error                    */
 #define MOR_ERR_STATE (-7)          /* handle used in the wrong state                  */
 
@@ -80,6 +82,26 @@ typedef struct {
 int mor_build_subdomains(const mor_mesh* mesh, const int32_t* owner, int32_t r_hops,
                          void* stream, mor_subdomains** out);
 
+/* A P1 tetrahedral mesh with every array in host memory (pinned memory makes the
+ * copies faster; pageable memory works too). */
+typedef struct {
+  int64_t n_nodes;
+  int64_t n_tets;
+  const int32_t* tets;       /* [host] n_tets x 4 vertex ids                            */
+  const uint8_t* dirichlet;  /* [host] n_nodes, 1 = node on the Dirichlet boundary      */
+  const double* xyz;         /* [host] n_nodes x 3 coordinates                          */
+  const double* kappa;       /* [host] n_tets coefficient k_T > 0                       */
+} mor_mesh_host;
+
+/* Step 1 from host arrays: as mor_build_subdomains (wave_subdomains = 0) or
+ * mor_build_subdomains_streamed (wave_subdomains > 0), but the library copies the
+ * coordinates, connectivity and coefficient to the device itself, on `stream`, into
+ * memory owned by the handle (freed by mor_free_subdomains).  The host arrays are only
+ * read during the call. */
+int mor_build_subdomains_host(const mor_mesh_host* mesh, const int32_t* owner,
+                              int32_t r_hops, int32_t wave_subdomains, void* stream,
+                              mor_subdomains** out);
+
 /* Step 1 for meshes whose per-subdomain structures do not fit at once (the 440^3
  * cube of 8000 subdomains: ~6e8 extended rows).  Builds and keeps only the global part
  * (owned DOFs, interface entries, node -> element incidence) plus host copies of the
@@ -106,6 +128,9 @@ int mor_subdomains_indices(const mor_subdomains* h, int32_t sub, int32_t which,
                            int32_t* out);
 
 #define MOR_SKETCH_FIELD 0 /* W = ((H^+)^{-1} L xi)_B, L L^T = H^+ element-wise       */
+#define MOR_SKETCH_PAPER 1 /* W = R_BB^{-1} S, S Gaussian on B, R_BB from a dense
+                              Cholesky factor of H^+ in [I; B] order (Sec. 6, Lemma 4.1);
+                              subdomains with |I| + |B| <= 6144, one-shot plans        */
 
 typedef struct {
   int32_t rank;        /* m: singular vectors kept per subdomain (fixed-rank mode)      */
@@ -116,7 +141,7 @@ typedef struct {
                           the k_i computed, instead of the first m_i                    */
   uint64_t seed;       /* Philox-4x32-10 key of the Gaussian draws                      */
   int32_t precision;   /* MOR_FP64 or MOR_MIXED                                         */
-  int32_t sketch;      /* MOR_SKETCH_FIELD                                              */
+  int32_t sketch;      /* MOR_SKETCH_FIELD or MOR_SKETCH_PAPER                          */
   double cg_rtol;      /* every local solve: ||b - A x||_2 <= cg_rtol ||b||_2 per column,
                           residual measured in binary64.  A column also stops when its
                           residual is below 4 u || |A| |x| + |b| ||_2 (u = 2^-53), the
@@ -151,11 +176,28 @@ typedef struct {
                           int grad w . grad v + w v of Sec. 4 (as printed); 1: its
                           gradient part is weighted by the coefficient k, a variant for
                           high contrast (the paper analyses k = 1, Sec. 7.3)           */
+  int32_t sketch_div;  /* > 0: subdomain i sketches k_i = max(1, floor(M_i / sketch_div))
+                          columns, M_i = |B_i| (the paper's k_i = floor(M_i / 8) with
+                          sketch_div = 8, Sec. 7.1 and App. C); needs eps > 0 (tolerance
+                          mode) and a one-shot plan; k_i <= 511.  0: k_i = m_i + p.    */
+  int32_t sub_begin;   /* streamed plans only: build the bases of subdomains            */
+  int32_t sub_end;     /* [sub_begin, sub_end) and leave the others empty (kept 0, Q and
+                          b~ zero), e.g. one GPU's share of a multi-GPU run or a sampled
+                          check; sub_end <= 0 means all.  The draws of a subdomain do
+                          not depend on the range.  One-shot plans require the whole
+                          range (MOR_ERR_ARG otherwise).                                */
+  int32_t explicit_svd; /* 1: the explicit weighted SVD of Eq. (14) instead of the
+                          randomized one: dense Cholesky factors of A_II, H_i and H^+
+                          (R_i, R_BB, Lemma 4.1), Z_i = C_i A_II^{-1} A_IB, and the
+                          singular vectors of R_i Z_i R_BB^{-1} (|B| <= 1024,
+                          |I| + |B| <= 6144, one-shot plans); rank / eps select the
+                          kept directions, sketch and oversample are not used          */
 } mor_basis_opts;
 
 /* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
  * max_iter 20000, replace_every 40, normwise 1, drift_restart 1.5, sketch_rtol 0,
- * tau 1e-12, orth_tol 1e-14, coarse_rows 100, h1_weighted 0). */
+ * tau 1e-12, orth_tol 1e-14, coarse_rows 100, h1_weighted 0, sketch_div 0, sub_begin 0,
+ * sub_end 0, explicit_svd 0). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 
 /* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (24)):
@@ -171,7 +213,8 @@ int mor_basis_opts_default(mor_basis_opts* opts);
 int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* opts, void* stream,
                     mor_bases** out);
 
-/* Sizes of step 2: *kq = columns stored per subdomain (>= max m_i + 1, multiple of 4),
+/* Sizes of step 2: *kq = columns stored per subdomain (>= max kept + 1, multiple of 4,
+ * at most 128),
  * *k = the largest sketch width k_i; kept[host, n_sub] = basis columns kept per
  * subdomain (may be NULL); *total_kept = sum of kept (may be NULL). */
 int mor_bases_info(const mor_bases* h, int32_t* kq, int32_t* k, int32_t* kept,
@@ -180,6 +223,12 @@ int mor_bases_info(const mor_bases* h, int32_t* kq, int32_t* k, int32_t* kept,
 /* sigma[host, n_sub x k]: the singular values of B (Eq. (24)) per subdomain, descending
  * (zeros beyond k_i). */
 int mor_bases_sigma(const mor_bases* h, double* sigma);
+
+/* R_BB of subdomain `sub` (Lemma 4.1: the trailing |B| x |B| block of the upper
+ * Cholesky factor of H^+ in [I; B] order, B in ascending node order) into
+ * out[host, |B| x |B|], row-major; only for bases built with MOR_SKETCH_PAPER or
+ * explicit_svd (MOR_ERR_STATE otherwise). */
+int mor_bases_get_rbb(const mor_bases* h, int32_t sub, double* out);
 
 /* Q_i of subdomain `sub` into out[host, |owned| x kq] (row-major; rows = owned dofs in
  * ascending node order, columns beyond kept[sub] are zero). */
@@ -216,7 +265,12 @@ typedef struct {
 } mor_solve_info;
 
 /* Step 3b: K~ x = b~ by CG with the diagonal (= identity) preconditioner, binary64.
- * x_dev [device, dim] is written.  info may be NULL. */
+ * x_dev [device, dim] is written.  info may be NULL.  The whole iteration runs in one
+ * cooperative launch (blocks over the block rows of K~, grid barriers between the
+ * phases of an iteration); every barrier wait is bounded by the wait budget
+ * (mor_set_wait_budget), and a wait that runs out ends the kernel with
+ * MOR_ERR_TIMEOUT instead of hanging.  Where a cooperative launch is not possible the
+ * same iteration runs as three launches per step. */
 int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void* stream,
                       double* x_dev, mor_solve_info* info);
 
@@ -233,12 +287,19 @@ int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void*
  *   kq x kq row-major blocks; the diagonal blocks are the identity and are not stored.
  *   bt_dev[n_sub * kq] is the reduced load.
  * Output [device, caller-owned]: x_dev[n_sub * kq].  info [host] may be NULL.
- * Work space: a fixed device array inside the library (about 12.5 MB: the three CG
- * vectors plus partial sums), held by every GPU that loads the library until the
- * process exits.  Limits: n_sub * kq <= 524288 and n_sub <= 65536; larger systems are
- * rejected with MOR_ERR_ARG and a message.
- * The first call on a device looks up the array's device address with that device
- * current and caches it; make that first call before any stream capture.
+ * Work space: a fixed device array inside the library (1,703,952 doubles = 13.6 MB:
+ * the three CG vectors plus partial sums).  It is placed on a device when the
+ * library's device code for this entry point is loaded there (with CUDA's default lazy
+ * module loading: during the first call on that device) and stays until the process
+ * exits.  Limits: n_sub * kq <= 524288 and n_sub <= 65536; larger systems are rejected
+ * with MOR_ERR_ARG and a message.
+ * Set-up: the first call on a device (and the first after that device's context was
+ * reset) looks up the array's device address with that device current and keeps it.
+ * That first call loads the module, which may allocate and synchronize inside the
+ * CUDA runtime: make it once at initialisation, before any stream capture.  Later
+ * calls on that device allocate nothing.
+ * The call waits for its stream every 16 iterations to read the convergence flag, and
+ * at the end to read the residual and energy.
  * Every call shares the one array and leaves its contents behind; the call clears the
  * state that must start at zero.  Calls whose GPU work overlaps (for example on two
  * streams, or two host threads) race on the array: serialise them.
@@ -249,6 +310,18 @@ int mor_solve_reduced_noalloc(int32_t n_sub, int32_t kq, const int32_t* nbr_ptr_
                               const double* blocks_dev, const double* bt_dev, double rtol,
                               int32_t max_iter, void* stream, double* x_dev,
                               mor_solve_info* info);
+
+/* Budget of every bounded device-side wait (grid barriers of mor_solve_reduced), in
+ * seconds of the GPU's SM clock (default 1 s; a barrier normally waits microseconds).
+ * Process-wide, not thread-safe.  The paper has no counterpart. */
+int mor_set_wait_budget(double seconds);
+
+/* Test of the timeout path: one thread waits, with the given budget in seconds, on a
+ * device flag that nothing sets.  *timed_out [host] = 1 when the wait ran out and the
+ * kernel returned (the expected outcome), 0 otherwise; returns MOR_ERR_TIMEOUT in the
+ * first case and MOR_OK in the second.  Allocates 16 bytes of device memory for the
+ * flag.  The paper has no counterpart. */
+int mor_debug_wait_timeout(double seconds, int32_t* timed_out);
 
 /* u~ = sum_i S_i Q_i x_i on all nodes (zero on the Dirichlet boundary):
  * x_dev [device, dim], u_dev [device, n_nodes]. */

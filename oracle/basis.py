@@ -132,14 +132,24 @@ def sketch_W(mesh, s, loc, k, seed, mode, R_BB=None):
 
 def local_basis(mesh, kappa, s, rank, oversample=0, seed=0, sketch="field",
                 explicit=False, eps=None, tau=1e-12, f=None, keep_all=False,
-                h1_weighted=False):
+                h1_weighted=False, rbb="auto"):
+    """rbb: "always" forms R_BB (Lemma 4.1) and takes the SVD of B of Eq. (24) as
+    printed; "never" (field sketch only) takes the same singular values and left
+    singular vectors from B B^T = T^T S_B^{-1} T with S_B^{-1} T = ((H^+)^{-1} [0; T])_B
+    (Lemma 4.1 and the block inverse of H^+), which avoids the dense Schur complement
+    of large subdomains; "auto" forms R_BB where the explicit SVD or the paper's sketch
+    needs it, or where H^+ is small enough for a dense Cholesky."""
     loc = local_system(mesh, kappa, s, f, h1_weighted)
     C, D = loc["C"], loc["D"]
     luA = splu(loc["A_II"])
     u0 = luA.solve(loc["b_I"])
     q0 = C @ u0
     R_i = np.linalg.cholesky(loc["H_i"].toarray()).T
-    R_BB = weight_rbb(loc["H_plus"], loc["nI"])
+    # R_BB (Lemma 4.1) enters the explicit SVD and the paper's sketch W = R_BB^{-1} S;
+    # the field sketch and the two left solves of the randomized path do not need it
+    need_rbb = explicit or sketch == "paper" or rbb == "always" or (
+        rbb == "auto" and loc["H_plus"].shape[0] <= 6000)
+    R_BB = weight_rbb(loc["H_plus"], loc["nI"]) if need_rbb else None
     out = dict(i=s["i"], nI=loc["nI"], nB=loc["nB"], n_omega=len(s["omega"]),
                owned=s["owned"], u0=u0)
     if explicit:
@@ -156,9 +166,23 @@ def local_basis(mesh, kappa, s, rank, oversample=0, seed=0, sketch="field",
         t1 = C.T @ (R_i.T @ Qh)                    # (Qh^T R_i C)^T
         t2 = luA.solve(t1, trans="T")              # A_II^{-T} (...)
         t3 = loc["A_IB"].T @ t2                    # ((...)^T A_IB)^T
-        t4 = sla.solve_triangular(R_BB, t3, trans="T")  # R_BB^{-T} (...)
-        Bm = t4.T
-        Uh, sig, _ = np.linalg.svd(Bm, full_matrices=False)
+        if R_BB is not None:
+            t4 = sla.solve_triangular(R_BB, t3, trans="T")  # R_BB^{-T} (...)
+            Bm = t4.T
+        else:
+            # B B^T = t3^T S_B^{-1} t3 with S_B = R_BB^T R_BB (Lemma 4.1), and
+            # S_B^{-1} t3 = ((H^+)^{-1} [0; t3])_B (block inverse of H^+): the same
+            # singular values and left singular vectors as B without forming R_BB
+            nI = loc["nI"]
+            g = splu(loc["H_plus"].tocsc()).solve(
+                np.vstack([np.zeros((nI, t3.shape[1])), t3]))[nI:]
+            G = t3.T @ g
+            lam, Uh = np.linalg.eigh(0.5 * (G + G.T))
+            lam, Uh = lam[::-1], Uh[:, ::-1]
+            sig = np.sqrt(np.maximum(lam, 0.0))
+            Bm = None
+        if Bm is not None:
+            Uh, sig, _ = np.linalg.svd(Bm, full_matrices=False)
         UU = Qh @ Uh
         out["W"] = W
     if eps is not None:

@@ -63,6 +63,44 @@ def subdomain_sets(mesh, owner, i, r_hops, adj=None):
                 omega_tets=omega_t)
 
 
+def subdomain_sets_region(mesh, owner, i, r_hops, region_tets):
+    """subdomain_sets computed from a candidate subset of the elements (global ids),
+    for meshes too large for a global adjacency.  The candidates must include every
+    element with a vertex within r + 1 edge hops of P_i: then the hop ball, T_i^+, the
+    element counts that split I from B, omega_i and the owned nodes are those of the
+    whole mesh, and the result equals subdomain_sets (global node and element ids)."""
+    region_tets = np.asarray(region_tets, dtype=np.int64)
+    T = mesh.tets[region_tets]
+    nodes, loc = np.unique(T, return_inverse=True)
+    loc = loc.reshape(T.shape)
+    nl = len(nodes)
+    P = owner[nodes] == i
+    if int(P.sum()) != int(np.count_nonzero(owner == i)):
+        raise ValueError("region does not contain every owned node")
+    r = np.repeat(loc, 4, axis=1).ravel()
+    c = np.tile(loc, (1, 4)).ravel()
+    adj = sp.coo_matrix((np.ones(len(r), dtype=np.int8), (r, c)), shape=(nl, nl)).tocsr()
+    ball = P.copy()
+    for _ in range(hops_for(int(P.sum()), r_hops)):
+        ball = ball | ((adj @ ball.astype(np.int8)) > 0)
+    plus_l = np.flatnonzero(ball[loc].any(axis=1))
+    omega_l = np.flatnonzero(P[loc].any(axis=1))
+    cnt_all = np.bincount(loc.ravel(), minlength=nl)
+    cnt_plus = np.bincount(loc[plus_l].ravel(), minlength=nl)
+    in_plus = cnt_plus > 0
+    interior = in_plus & (cnt_plus == cnt_all)
+    free = mesh.dirichlet[nodes] == 0
+    in_omega = np.bincount(loc[omega_l].ravel(), minlength=nl) > 0
+    if not np.all(interior[in_omega & free]):
+        raise ValueError("omega_i is not interior to omega_i^+ (need r_hops >= 1)")
+    # global ids ascending: nodes are sorted, and so are the candidate element ids
+    pl = np.sort(region_tets[plus_l])
+    ol = np.sort(region_tets[omega_l])
+    return dict(i=i, I=nodes[interior & free], B=nodes[in_plus & ~interior & free],
+                omega=nodes[in_omega & free], owned=nodes[P & free], plus_tets=pl,
+                omega_tets=ol)
+
+
 def all_subdomains(mesh, owner, r_hops):
     adj = node_adjacency(mesh.tets, mesh.n_nodes)
     n_sub = int(owner.max()) + 1

@@ -177,6 +177,16 @@ struct Prof {
 Prof g_prof;
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// budget of the bounded device-side waits, seconds of SM clock
+double g_wait_budget_s = 1.0;
+long long wait_budget_cycles() {
+  int dev = 0, khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (khz <= 0) khz = 2000000;
+  return (long long)(g_wait_budget_s * 1e3 * (double)khz);
+}
 int round_up4(int x) { return (x + 3) & ~3; }
 
 }  // namespace
@@ -218,6 +228,10 @@ struct mor_subdomains_s {
 struct mor_bases_s {
   int n_sd = 0, k = 0, kp = 0, kq = 0, m = 0;
   Allocs mem;
+  // R_BB per subdomain (paper sketch or explicit SVD only)
+  double* Rbb = nullptr;
+  std::vector<int64_t> rbb_off;
+  std::vector<int32_t> rbb_m;
   double *Q = nullptr, *bt = nullptr, *sigma = nullptr;
   int* kept = nullptr;
   std::vector<int32_t> h_kept;
@@ -377,6 +391,61 @@ int mor_build_subdomains_streamed(const mor_mesh* mesh, const int32_t* owner, in
   return MOR_OK;
 }
 
+int mor_build_subdomains_host(const mor_mesh_host* mesh, const int32_t* owner,
+                              int32_t r_hops, int32_t wave_subdomains, void* stream,
+                              mor_subdomains** out) {
+  if (!mesh || !owner || !out || !mesh->tets || !mesh->dirichlet || !mesh->xyz ||
+      !mesh->kappa || mesh->n_nodes < 1 || mesh->n_tets < 1 || wave_subdomains < 0)
+    return fail(MOR_ERR_ARG, "mor_build_subdomains_host: bad argument");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto h = std::make_unique<mor_subdomains_s>();
+  // device copies owned by the handle; the host -> device copies overlap step 1 on the
+  // host, which reads the host arrays directly
+  double *xyz_d, *kappa_d;
+  int32_t* tets_d;
+  Allocs& A = h->mem;
+  TRY(A.alloc(&xyz_d, (size_t)mesh->n_nodes * 3, false, st));
+  TRY(A.alloc(&tets_d, (size_t)mesh->n_tets * 4, false, st));
+  TRY(A.alloc(&kappa_d, (size_t)mesh->n_tets, false, st));
+  CK(cudaMemcpyAsync(xyz_d, mesh->xyz, (size_t)mesh->n_nodes * 3 * sizeof(double),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(tets_d, mesh->tets, (size_t)mesh->n_tets * 4 * sizeof(int32_t),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(kappa_d, mesh->kappa, (size_t)mesh->n_tets * sizeof(double),
+                     cudaMemcpyHostToDevice, st));
+  std::string err;
+  int rc;
+  if (wave_subdomains > 0) {
+    rc = build_global_plan(mesh->n_nodes, mesh->n_tets, mesh->tets, mesh->dirichlet, owner,
+                           r_hops, h->hp, err);
+    if (rc != MOR_OK) {
+      cudaStreamSynchronize(st);  // the copies read the caller's arrays
+      return fail(rc, err);
+    }
+    h->streamed = true;
+    h->wave_sd = wave_subdomains;
+    h->h_tets.assign(mesh->tets, mesh->tets + 4 * mesh->n_tets);
+    h->h_dir.assign(mesh->dirichlet, mesh->dirichlet + mesh->n_nodes);
+    h->h_xyz.assign(mesh->xyz, mesh->xyz + 3 * mesh->n_nodes);
+  } else {
+    rc = build_host_plan(mesh->n_nodes, mesh->n_tets, mesh->tets, mesh->dirichlet, owner,
+                         r_hops, mesh->xyz, h->hp, err);
+    if (rc != MOR_OK) {
+      cudaStreamSynchronize(st);
+      return fail(rc, err);
+    }
+  }
+  h->xyz = xyz_d;
+  h->tets = tets_d;
+  h->kappa = kappa_d;
+  if (!h->streamed) TRY(upload_heavy(h.get(), st));
+  TRY(upload_light(h.get(), st));
+  CK(cudaStreamSynchronize(st));
+  *out = h.release();
+  return MOR_OK;
+}
+
 int mor_subdomains_counts(const mor_subdomains* h, int32_t* n_sub_out, int64_t* counts) {
   if (!h) return fail(MOR_ERR_ARG, "mor_subdomains_counts: null handle");
   if (n_sub_out) *n_sub_out = h->hp.n_sd;
@@ -436,6 +505,10 @@ int mor_basis_opts_default(mor_basis_opts* o) {
   o->orth_tol = 1e-14;
   o->coarse_rows = 100;
   o->h1_weighted = 0;
+  o->sketch_div = 0;
+  o->explicit_svd = 0;
+  o->sub_begin = 0;
+  o->sub_end = 0;
   return MOR_OK;
 }
 
@@ -609,6 +682,90 @@ struct Build {
 
 };
 
+// ---- paper-literal weights (Lemma 4.1, Eq. (14)) with dense per-subdomain factors ----
+// Dense H^+ in [I; B] order (I rows in the plan's order, B rows in ascending node order,
+// the order of the oracle), its Cholesky factor, and the factor's trailing block L_BB
+// with R_BB = L_BB^T (Lemma 4.1: R_BB^T R_BB = S_B).
+struct DenseWeights {
+  int n_sd = 0, n_max = 0, m_max = 0, i_max = 0;
+  std::vector<int32_t> h_nI, h_M, h_nH;
+  std::vector<int64_t> h_boff, h_bboff;
+  int32_t *p_loc = nullptr, *nI = nullptr, *M = nullptr, *nH = nullptr, *zero = nullptr;
+  int32_t *bnode = nullptr, *bprow = nullptr;
+  int64_t *hoff = nullptr, *boff = nullptr, *bboff = nullptr;
+  double *H = nullptr, *Lbb = nullptr, *Rbb = nullptr;
+};
+
+// dense problems above this order are refused (the dense path serves small subdomains,
+// as the paper's explicit SVD does)
+constexpr int kDenseMaxOrder = 6144;
+
+int dense_weights(const HostPlan& hp, const int32_t* p_sd_dev, Allocs& Mem,
+                  const EllView<double>& Hp, DenseWeights& D, cudaStream_t st) {
+  const int n_sd = hp.n_sd;
+  D.n_sd = n_sd;
+  D.h_nI.resize(n_sd);
+  D.h_M.resize(n_sd);
+  D.h_nH.resize(n_sd);
+  std::vector<int32_t> p_loc(hp.nP), bnode, bprow;
+  std::vector<int64_t> hoff(n_sd + 1, 0), boff(n_sd + 1, 0), bboff(n_sd + 1, 0);
+  for (int i = 0; i < n_sd; ++i) {
+    const int nI = hp.nI[i], nB = hp.nB[i];
+    const int64_t P0 = hp.Poff[i];
+    D.h_nI[i] = nI;
+    D.h_M[i] = nB;
+    D.h_nH[i] = nI + nB;
+    if (nI + nB > kDenseMaxOrder)
+      return fail(MOR_ERR_ARG, "mor_build_bases: paper-literal weights need |I| + |B| <= " +
+                                   std::to_string(kDenseMaxOrder) + " (dense factors)");
+    D.n_max = std::max(D.n_max, nI + nB);
+    D.m_max = std::max(D.m_max, nB);
+    D.i_max = std::max(D.i_max, nI);
+    for (int l = 0; l < nI; ++l) p_loc[P0 + l] = l;
+    std::vector<std::pair<int32_t, int64_t>> b(nB);
+    for (int l = 0; l < nB; ++l) b[l] = {hp.p_node[P0 + nI + l], P0 + nI + l};
+    std::sort(b.begin(), b.end());
+    for (int l = 0; l < nB; ++l) {
+      p_loc[b[l].second] = nI + l;
+      bnode.push_back(b[l].first);
+      bprow.push_back((int32_t)b[l].second);
+    }
+    hoff[i + 1] = hoff[i] + (int64_t)(nI + nB) * (nI + nB);
+    boff[i + 1] = boff[i] + nB;
+    bboff[i + 1] = bboff[i] + (int64_t)nB * nB;
+  }
+  D.h_boff = boff;
+  D.h_bboff = bboff;
+  std::vector<int32_t> zero(n_sd, 0);
+  TRY(Mem.upload(&D.p_loc, p_loc, st));
+  TRY(Mem.upload(&D.nI, D.h_nI, st));
+  TRY(Mem.upload(&D.M, D.h_M, st));
+  TRY(Mem.upload(&D.nH, D.h_nH, st));
+  TRY(Mem.upload(&D.zero, zero, st));
+  TRY(Mem.upload(&D.bnode, bnode, st));
+  TRY(Mem.upload(&D.bprow, bprow, st));
+  TRY(Mem.upload(&D.hoff, hoff, st));
+  TRY(Mem.upload(&D.boff, boff, st));
+  TRY(Mem.upload(&D.bboff, bboff, st));
+  TRY(Mem.alloc(&D.H, (size_t)hoff[n_sd], true, st));
+  TRY(Mem.alloc(&D.Lbb, (size_t)std::max<int64_t>(bboff[n_sd], 1), true, st));
+  TRY(Mem.alloc(&D.Rbb, (size_t)std::max<int64_t>(bboff[n_sd], 1), true, st));
+  // dense H^+ of every subdomain (order nH = nI + nB), its Cholesky factor in place
+  launch_ell_to_dense(hp.nP, p_sd_dev, D.p_loc, D.p_loc, Hp, D.zero, D.nH, D.zero, D.nH, D.nH,
+                      D.hoff, D.H, st);
+  int* bad;
+  TRY(Mem.alloc(&bad, 1, true, st));
+  launch_potrf(n_sd, D.n_max, D.H, D.hoff, D.nH, bad, st);
+  // L_BB = the trailing nB x nB block of the factor, R_BB = L_BB^T
+  launch_transpose_block(n_sd, D.m_max, D.H, D.hoff, D.nH, D.nI, D.M, D.Lbb, D.bboff, 0, st);
+  launch_transpose_block(n_sd, D.m_max, D.H, D.hoff, D.nH, D.nI, D.M, D.Rbb, D.bboff, 1, st);
+  int h_bad = 0;
+  CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h_bad) return fail(MOR_ERR_CUDA, "mor_build_bases: H^+ is not positive definite");
+  return MOR_OK;
+}
+
 }  // namespace
 
 // step 2 for every subdomain of a plan whose per-subdomain part is on the device;
@@ -619,27 +776,49 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   *out = nullptr;
   const mor_basis_opts& o = *opts;
   const int n_sd_h = sd->hp.n_sd;
+  const bool tol_mode = o.eps > 0.0;
+  if (o.sketch_div < 0) return fail(MOR_ERR_ARG, "mor_build_bases: sketch_div must be >= 0");
+  if (o.sketch_div > 0 && (!tol_mode || m_force > 0))
+    return fail(MOR_ERR_ARG, "mor_build_bases: sketch_div needs eps > 0 and a one-shot plan");
   std::vector<int32_t> h_rank(n_sd_h), h_k(n_sd_h);
   for (int i = 0; i < n_sd_h; ++i) h_rank[i] = o.ranks ? o.ranks[i] : o.rank;
   int m_max = 0;
   for (int i = 0; i < n_sd_h; ++i) {
-    if (h_rank[i] < 1 || o.oversample < 0)
-      return fail(MOR_ERR_ARG, "mor_build_bases: ranks >= 1 and oversample >= 0 required");
-    h_k[i] = h_rank[i] + o.oversample;
-    m_max = std::max(m_max, h_rank[i]);
+    if (o.sketch_div > 0) {
+      // the paper's sketch size k_i = floor(M_i / 8) (Sec. 7.1): sigma_j > eps among
+      // them are kept, so the rank entry is not used
+      h_k[i] = std::max(1, sd->hp.nB[i] / o.sketch_div);
+      h_rank[i] = h_k[i];
+    } else {
+      if (h_rank[i] < 1 || o.oversample < 0)
+        return fail(MOR_ERR_ARG, "mor_build_bases: ranks >= 1 and oversample >= 0 required");
+      h_k[i] = h_rank[i] + o.oversample;
+    }
+    m_max = std::max(m_max, o.sketch_div > 0 ? h_k[i] : h_rank[i]);
   }
   if (m_force > 0) m_max = std::max(m_max, m_force);
-  const int k = m_max + o.oversample;     // widest sketch; the load column sits at k
+  // widest sketch; the load column sits at k
+  const int k = o.sketch_div > 0 ? m_max : m_max + o.oversample;
   const int kp = round_up4(k + 1);
-  const bool tol_mode = o.eps > 0.0;
-  const int kq = round_up4((tol_mode ? k : m_max) + 1);
-  const int mcols = kq - 1 < (tol_mode ? k : m_max) ? kq - 1 : (tol_mode ? k : m_max);
-  if (kp > 80 || kq > 80)
-    return fail(MOR_ERR_ARG, "mor_build_bases: rank + oversample must be <= 79");
+  // columns per subdomain kept for the reduced system: fixed rank m_max + 1; in
+  // tolerance mode the widest kept count + 1, known after the weighted SVD (at most k)
+  int kq = round_up4((tol_mode ? k : m_max) + 1);
+  int mcols = tol_mode ? k : m_max;
+  const bool wide = kp > 80;
+  if (kp > 512)
+    return fail(MOR_ERR_ARG, "mor_build_bases: sketch width must be <= 511 columns");
+  if (!tol_mode && kq > 128)
+    return fail(MOR_ERR_ARG, "mor_build_bases: rank + 1 must be <= 128 basis columns");
   if (!(o.eps >= 0.0)) return fail(MOR_ERR_ARG, "mor_build_bases: eps must be >= 0");
   if (o.precision != MOR_FP64 && o.precision != MOR_MIXED)
     return fail(MOR_ERR_ARG, "mor_build_bases: unknown precision");
-  if (o.sketch != MOR_SKETCH_FIELD) return fail(MOR_ERR_ARG, "mor_build_bases: unknown sketch");
+  if (o.sketch != MOR_SKETCH_FIELD && o.sketch != MOR_SKETCH_PAPER)
+    return fail(MOR_ERR_ARG, "mor_build_bases: unknown sketch");
+  const bool dense = o.sketch == MOR_SKETCH_PAPER || o.explicit_svd != 0;
+  if (dense && m_force > 0)
+    return fail(MOR_ERR_ARG, "mor_build_bases: paper-literal weights need a one-shot plan");
+  if (o.explicit_svd && o.sketch_div > 0)
+    return fail(MOR_ERR_ARG, "mor_build_bases: explicit_svd has no sketch (sketch_div)");
   if (!(o.cg_rtol > 0.0) || o.max_iter < 1 || o.replace_every < 1 || !(o.drift_restart >= 1.0))
     return fail(MOR_ERR_ARG, "mor_build_bases: bad solver tolerances");
 
@@ -791,6 +970,10 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
       }
   }
 
+  // ---- paper-literal weights: dense H^+ factor, R_BB (Lemma 4.1) ----
+  DenseWeights DW;
+  if (dense) TRY(dense_weights(hp, S.p_sd, M, Hp.e64(), DW, st));
+
   // ---- solver workspace ----
   size_t tsz = B.mixed ? sizeof(float) : sizeof(double);
   double *vS, *vG, *vF, *vX;
@@ -860,34 +1043,65 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   }
   TRY(M.alloc(&B.rs.counter, n_sd, true, st));
   TRY(M.alloc(&B.rs.active, n_sd, true, st));
-  double *Xw, *Yw, *Zw, *u0w, *V, *AV, *bP;
+  double *Xw, *Yw, *Zw, *u0w, *V = nullptr, *AV = nullptr, *bP;
   TRY(M.alloc(&Xw, nW * kp, true, st));
   TRY(M.alloc(&Yw, nW * kp, true, st));
   TRY(M.alloc(&Zw, nW * kp, true, st));
   TRY(M.alloc(&u0w, nW, true, st));
-  TRY(M.alloc(&V, nO * kq, true, st));
-  TRY(M.alloc(&AV, nO * kq, true, st));
   TRY(M.alloc(&bP, nO, true, st));
-  double *G, *evals, *evecs, *Mm, *gpart;
+  double *G, *evals, *evecs, *Mm, *gpart, *eigw = nullptr;
   int *gcnt, *kcnt;
-  TRY(M.alloc(&G, (size_t)n_sd * kp * kp, true, st));
-  TRY(M.alloc(&evals, (size_t)n_sd * kp, true, st));
-  TRY(M.alloc(&evecs, (size_t)n_sd * kp * kp, true, st));
-  TRY(M.alloc(&Mm, (size_t)n_sd * kp * kp, true, st));
-  TRY(M.alloc(&gpart, (size_t)mt * kp * kp, true, st));
+  // the k x k work of the sketch and the diagonal-block update on kq <= 128 columns;
+  // the explicit SVD can keep more columns than its (unused) sketch width
+  const int kb = o.explicit_svd ? std::max(kp, 128) : kp;
+  TRY(M.alloc(&G, (size_t)n_sd * kb * kb, true, st));
+  TRY(M.alloc(&evals, (size_t)n_sd * kb, true, st));
+  TRY(M.alloc(&evecs, (size_t)n_sd * kb * kb, true, st));
+  TRY(M.alloc(&Mm, (size_t)n_sd * kb * kb, true, st));
+  {
+    // Gram partials: per row tile for the small Grams (at most 80 x 80), per row chunk
+    // of a subdomain for the wide ones
+    const size_t nk = (size_t)std::min(kb, 80);
+    size_t gsz = (size_t)mt * nk * nk;
+    if (wide || kb > 80) {
+      // the sketch Grams (k x k) and the diagonal-block Gram (at most 128 x 128)
+      gsz = std::max(gsz, (size_t)n_sd * gram_wide_chunks(n_sd, k, k) * k * k);
+      gsz = std::max(gsz, (size_t)n_sd * 16 * 128 * 128);
+      TRY(M.alloc(&eigw, (size_t)n_sd * 2 * kb * kb, false, st));
+    }
+    TRY(M.alloc(&gpart, gsz, true, st));
+  }
   TRY(M.alloc(&gcnt, n_sd, true, st));
   TRY(M.alloc(&kcnt, n_sd, true, st));
+  // the small kernels serve widths up to 80 columns, the wide ones the rest
+  auto gram = [&](const DTiles& tl, const double* X, int ldx, int nx, const double* Y,
+                  int ldy, int ny, int ldg) {
+    if (nx > 80 || ny > 80)
+      launch_gram_wide(tl, n_sd, X, ldx, nx, Y, ldy, ny, gpart, G, ldg, (int64_t)ldg * ldg,
+                       st);
+    else
+      launch_gram(tl, n_sd, X, ldx, nx, Y, ldy, ny, gpart, gcnt, G, ldg, st);
+  };
+  auto sym_eig = [&](int ld, int n, double* ev, double* V_) {
+    if (n > 80)
+      launch_sym_eig_wide(n_sd, G, ld, n, ev, V_, eigw, st);
+    else
+      launch_sym_eig(n_sd, G, ld, n, ev, V_, st);
+  };
+  auto rowmul = [&](const DTiles& tl, const double* X, int ldx, int nin, int ldm, double* Y,
+                    int ldy, int nout) {
+    if (nin > 80 || nout > 80 || ldy > 80)
+      launch_rowmul_wide(tl, X, ldx, nin, Mm, ldm, Y, ldy, nout, st);
+    else
+      launch_rowmul(tl, X, ldx, nin, Mm, ldm, Y, ldy, nout, st);
+  };
 
   auto bases = std::make_unique<mor_bases_s>();
   mor_bases_s& Bo = *bases;
   Bo.n_sd = n_sd;
   Bo.k = k;
   Bo.kp = kp;
-  Bo.kq = kq;
-  Bo.m = mcols;
   Bo.Ooff = hp.Ooff;
-  TRY(Bo.mem.alloc(&Bo.Q, nO * kq, true, st));
-  TRY(Bo.mem.alloc(&Bo.bt, (size_t)n_sd * kq, true, st));
   TRY(Bo.mem.alloc(&Bo.sigma, (size_t)n_sd * kp, true, st));
   TRY(Bo.mem.alloc(&Bo.kept, n_sd, true, st));
 
@@ -909,64 +1123,246 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   TRY(M.upload(&d_ksd, h_k, st));
   TRY(M.upload(&d_msd, h_rank, st));
   TRY(M.alloc(&d_msel, n_sd, true, st));
-  launch_sketch_rhs(0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lsplit, k, o.seed,
-                    (uint32_t)S.sd_base, vS, kp, st, d_ksd);
-  TRY(solve(S.tP_all, Hp, false, vS, vG, k, 0, rt_sketch));
+  // the reduced system stores the widest kept count + 1 columns per subdomain (tolerance
+  // mode), and the output buffers are sized once that count is known
+  auto finish_kq = [&]() -> int {
+    if (tol_mode && m_force == 0) {
+      // the reduced system stores the widest kept count + 1 columns per subdomain
+      std::vector<int> msel(n_sd);
+      CK(cudaMemcpyAsync(msel.data(), d_msel, n_sd * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      mcols = 0;
+      for (int v : msel) mcols = std::max(mcols, v);
+      kq = round_up4(mcols + 1);
+    }
+    if (kq > 128)
+      return fail(MOR_ERR_ARG, "mor_build_bases: more than 127 singular values above eps in a "
+                               "subdomain (at most 128 basis columns per subdomain)");
+    B.kq = kq;
+    B.m = mcols;
+    Bo.kq = kq;
+    Bo.m = mcols;
+    TRY(M.alloc(&V, nO * kq, true, st));
+    TRY(M.alloc(&AV, nO * kq, true, st));
+    TRY(Bo.mem.alloc(&Bo.Q, nO * kq, true, st));
+    TRY(Bo.mem.alloc(&Bo.bt, (size_t)n_sd * kq, true, st));
+    return MOR_OK;
+  };
+  const double* colsW = Zw;  // X^ U_m (or R_i^{-1} U_m), W rows
+  int colsLd = kp;
+  // Eq. (14) explicitly, with dense factors: Z_I = A_II^{-1} [A_IB | b_I] (the last
+  // column is u_0 of Prob. "aux1"), Z = C_i Z_I, Y = R_i Z with R_i = chol(H_i)^T,
+  // X = Y R_BB^{-1}, and the SVD X = U Sigma V^T through eig(X^T X) = V Sigma^2 V^T;
+  // the basis columns are R_i^{-1} U_m with U_m = X V_m Sigma_m^{-1}
+  auto explicit_svd_bases = [&]() -> int {
+    const int mB = DW.m_max, iM = DW.i_max;
+    if (mB > 1024)
+      return fail(MOR_ERR_ARG, "mor_build_bases: explicit_svd needs |B| <= 1024");
+    const int ldz = mB + 1, ldm = round_up4(std::max(mB, 1));
+    std::vector<int64_t> aoff(n_sd + 1, 0), zoff(n_sd), woff(n_sd), hioff(n_sd + 1, 0);
+    std::vector<int32_t> nWsd(n_sd), ldz_v(n_sd, ldz), ncz(n_sd, ldz);
+    int w_max = 0;
+    for (int i = 0; i < n_sd; ++i) {
+      aoff[i + 1] = aoff[i] + (int64_t)DW.h_nI[i] * DW.h_nI[i];
+      zoff[i] = hp.Poff[i] * ldz;
+      woff[i] = hp.Woff[i];
+      nWsd[i] = (int32_t)(hp.Woff[i + 1] - hp.Woff[i]);
+      w_max = std::max(w_max, nWsd[i]);
+      hioff[i + 1] = hioff[i] + (int64_t)nWsd[i] * nWsd[i];
+    }
+    if (w_max > kDenseMaxOrder)
+      return fail(MOR_ERR_ARG, "mor_build_bases: explicit_svd needs |omega_i| <= 6144");
+    std::vector<int32_t> w_loc(nW), w_sdv(nW), w_row(nW);
+    for (int i = 0; i < n_sd; ++i)
+      for (int64_t r = hp.Woff[i]; r < hp.Woff[i + 1]; ++r) {
+        w_loc[r] = (int32_t)(r - hp.Woff[i]);
+        w_sdv[r] = i;
+        w_row[r] = (int32_t)(r - hp.Woff[i]);
+      }
+    std::vector<int64_t> poff(hp.Poff.begin(), hp.Poff.begin() + n_sd);
+    int64_t *d_aoff, *d_zoff, *d_woff, *d_hioff, *d_poff;
+    int32_t *d_nW, *d_ldz, *d_ncz, *d_wloc, *d_wsd, *d_wrow;
+    TRY(M.upload(&d_aoff, aoff, st));
+    TRY(M.upload(&d_zoff, zoff, st));
+    TRY(M.upload(&d_woff, woff, st));
+    TRY(M.upload(&d_hioff, hioff, st));
+    TRY(M.upload(&d_poff, poff, st));
+    TRY(M.upload(&d_nW, nWsd, st));
+    TRY(M.upload(&d_ldz, ldz_v, st));
+    TRY(M.upload(&d_ncz, ncz, st));
+    TRY(M.upload(&d_wloc, w_loc, st));
+    TRY(M.upload(&d_wsd, w_sdv, st));
+    TRY(M.upload(&d_wrow, w_row, st));
+    int* bad;
+    TRY(M.alloc(&bad, 1, true, st));
+    // A_II = L_A L_A^T (dense), U_A = L_A^T
+    double *Ad, *UA, *Zi, *Zw2, *Yw2, *Hd, *Ui, *Um;
+    TRY(M.alloc(&Ad, (size_t)std::max<int64_t>(aoff[n_sd], 1), true, st));
+    TRY(M.alloc(&UA, (size_t)std::max<int64_t>(aoff[n_sd], 1), true, st));
+    launch_ell_to_dense(nP, S.p_sd, DW.p_loc, DW.p_loc, A_II.e64(), DW.zero, DW.nI, DW.zero,
+                        DW.nI, DW.nI, d_aoff, Ad, st);
+    launch_potrf(n_sd, iM, Ad, d_aoff, DW.nI, bad, st);
+    launch_transpose_block(n_sd, iM, Ad, d_aoff, DW.nI, DW.zero, DW.nI, UA, d_aoff, 1, st);
+    // [A_IB | b_I] on the I rows of the P space (columns: B in ascending node order)
+    TRY(M.alloc(&Zi, (size_t)nP * ldz, true, st));
+    launch_ell_to_dense(nP, S.p_sd, DW.p_loc, DW.p_loc, A_IB.e64(), DW.zero, DW.nI, DW.nI,
+                        DW.M, d_ldz, d_zoff, Zi, st);
+    launch_set_col(S.tP_I, loadP, Zi, ldz, mB, st);
+    // A_II Z_I = [A_IB | b_I]: forward with L_A (column j = row j of U_A), backward
+    // with U_A (column j = row j of L_A)
+    launch_trsv_cols(n_sd, iM, ldz, UA, d_aoff, DW.nI, DW.nI, DW.zero, Zi, d_poff, ldz, d_ncz,
+                     1, st);
+    launch_trsv_cols(n_sd, iM, ldz, Ad, d_aoff, DW.nI, DW.nI, DW.zero, Zi, d_poff, ldz, d_ncz,
+                     0, st);
+    launch_gather_rows(nW, S.w2p, Zi, ldz, mB, u0w, 1, 0, 1, st);
+    TRY(M.alloc(&Zw2, (size_t)nW * ldm, true, st));
+    TRY(M.alloc(&Yw2, (size_t)nW * ldm, true, st));
+    launch_gather_rows(nW, S.w2p, Zi, ldz, 0, Zw2, ldm, 0, mB, st);
+    // H_i = L_i L_i^T (dense, W order), R_i = U_i = L_i^T; Y = R_i Z
+    TRY(M.alloc(&Hd, (size_t)std::max<int64_t>(hioff[n_sd], 1), true, st));
+    TRY(M.alloc(&Ui, (size_t)std::max<int64_t>(hioff[n_sd], 1), true, st));
+    launch_ell_to_dense(nW, d_wsd, d_wloc, d_wloc, Hi.e64(), DW.zero, d_nW, DW.zero, d_nW, d_nW,
+                        d_hioff, Hd, st);
+    launch_potrf(n_sd, w_max, Hd, d_hioff, d_nW, bad, st);
+    launch_transpose_block(n_sd, w_max, Hd, d_hioff, d_nW, DW.zero, d_nW, Ui, d_hioff, 1, st);
+    launch_trmv_upper(n_sd, w_max, mB, Ui, d_hioff, d_nW, Zw2, Yw2, d_woff, ldm, DW.M, st);
+    // X = Y R_BB^{-1}, one W row per warp
+    launch_trsv_rows(DW.Rbb, DW.bboff, DW.M, Yw2, d_woff, ldm, d_wsd, d_wrow, (int)nW, st);
+    int h_bad = 0;
+    CK(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_bad)
+      return fail(MOR_ERR_CUDA, "mor_build_bases: A_II or H_i is not positive definite");
+    // X^T X = V Sigma^2 V^T (binary64 Jacobi); sigma_j^2 stored like the randomized path's
+    double *Gx, *evx, *Vx, *Mx, *gp, *ew = nullptr;
+    TRY(M.alloc(&Gx, (size_t)n_sd * ldm * ldm, true, st));
+    TRY(M.alloc(&evx, (size_t)n_sd * ldm, true, st));
+    TRY(M.alloc(&Vx, (size_t)n_sd * ldm * ldm, true, st));
+    TRY(M.alloc(&Mx, (size_t)n_sd * ldm * ldm, true, st));
+    TRY(M.alloc(&gp, (size_t)std::max<int64_t>(
+                         (int64_t)n_sd * gram_wide_chunks(n_sd, mB, mB) * mB * mB,
+                         (int64_t)mt * std::min(ldm, 80) * std::min(ldm, 80)), true, st));
+    if (mB > 80) {
+      launch_gram_wide(S.tW, n_sd, Yw2, ldm, mB, Yw2, ldm, mB, gp, Gx, ldm, (int64_t)ldm * ldm,
+                       st);
+      TRY(M.alloc(&ew, (size_t)n_sd * 2 * ldm * ldm, false, st));
+      launch_sym_eig_wide(n_sd, Gx, ldm, mB, evx, Vx, ew, st);
+    } else {
+      launch_gram(S.tW, n_sd, Yw2, ldm, mB, Yw2, ldm, mB, gp, gcnt, Gx, ldm, st);
+      launch_sym_eig(n_sd, Gx, ldm, mB, evx, Vx, st);
+    }
+    // kept directions: the first m_i, or sigma_j > eps (Eq. (15)); U_m = X V_m Sigma_m^-1
+    std::vector<int32_t> keep(n_sd);
+    for (int i = 0; i < n_sd; ++i) keep[i] = tol_mode ? DW.h_M[i] : h_rank[i];
+    int32_t* d_keep;
+    TRY(M.upload(&d_keep, keep, st));
+    if (tol_mode)
+      launch_make_M(n_sd, 4, evx, Vx, ldm, mB, o.eps * o.eps, mB, Mx, d_msel, st, d_keep);
+    else
+      launch_make_M(n_sd, 3, evx, Vx, ldm, mB, 0.0, mB, Mx, d_msel, st, d_keep);
+    if (!tol_mode) mcols = std::min(m_max, mB);
+    TRY(finish_kq());
+    TRY(M.alloc(&Um, (size_t)nW * ldm, true, st));
+    launch_rowmul_wide(S.tW, Yw2, ldm, mB, Mx, ldm, Um, ldm, mcols, st);
+    // basis columns R_i^{-1} U_m: backward substitution with U_i (column j = row j of L_i)
+    launch_trsv_cols(n_sd, w_max, mcols, Hd, d_hioff, d_nW, d_nW, DW.zero, Um, d_woff, ldm,
+                     d_msel, 0, st);
+    colsW = Um;
+    colsLd = ldm;
+    // singular values: the explicit path reports all |B_i| of them
+    Bo.k = mB;
+    Bo.kp = ldm;
+    TRY(Bo.mem.alloc(&Bo.sigma, (size_t)n_sd * ldm, true, st));
+    CK(cudaMemcpyAsync(Bo.sigma, evx, (size_t)n_sd * ldm * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+    return MOR_OK;
+  };
+  if (o.explicit_svd) {
+    TRY(explicit_svd_bases());
+  } else {
+    if (o.sketch == MOR_SKETCH_PAPER) {
+      // W = R_BB^{-1} S (Sec. 6): S Gaussian on B (rows in ascending node order), a
+      // backward substitution with R_BB (its column j is row j of L_BB), then W goes to
+      // the B rows of the P space
+      double* Sb;
+      TRY(M.alloc(&Sb, (size_t)std::max<int64_t>(DW.h_boff[n_sd], 1) * k, true, st));
+      launch_node_normals(n_sd, DW.m_max, DW.bnode, DW.boff, DW.M, d_ksd, k, o.seed,
+                          (uint32_t)S.sd_base, Sb, k, st);
+      launch_trsv_cols(n_sd, DW.m_max, k, DW.Lbb, DW.bboff, DW.M, DW.M, DW.zero, Sb, DW.boff,
+                       k, d_ksd, 0, st);
+      CK(cudaMemsetAsync(vG, 0, nP * kp * sizeof(double), st));
+      launch_scatter_rows(DW.h_boff[n_sd], DW.bprow, Sb, k, vG, kp, k, st);
+    } else {
+      launch_sketch_rhs(0, nP, S.p_sd, S.incP_ptr, S.incP_tet, S.incP_code, lsplit, k, o.seed,
+                        (uint32_t)S.sd_base, vS, kp, st, d_ksd);
+      TRY(solve(S.tP_all, Hp, false, vS, vG, k, 0, rt_sketch));
+    }
 
-  // ---- forward solve A_II [X | u_0] = [A_IB W | b_I] (Prob. "aux1", Eq. (7), and the lifting of Eq. (8)) ----
-  launch_spmm<double>(S.tP_I, A_IB.e64(), vG, vF, kp, st);
-  launch_set_col(S.tP_I, loadP, vF, kp, k, st);
-  TRY(solve(S.tP_I, A_II, true, vF, vX, k + 1, 1, rt));
+    // ---- forward solve A_II [X | u_0] = [A_IB W | b_I] (Prob. "aux1", Eq. (7), and the lifting of Eq. (8)) ----
+    launch_spmm<double>(S.tP_I, A_IB.e64(), vG, vF, kp, st);
+    launch_set_col(S.tP_I, loadP, vF, kp, k, st);
+    TRY(solve(S.tP_I, A_II, true, vF, vX, k + 1, 1, rt));
 
-  // ---- X = C_i X_full, orthonormalise in the H_i inner product (twice) ----
-  launch_gather_rows(nW, S.w2p, vX, kp, 0, Xw, kp, 0, kp, st);
-  launch_gather_rows(nW, S.w2p, vX, kp, k, u0w, 1, 0, 1, st);
-  for (int pass = 0; pass < 2; ++pass) {
+    // ---- X = C_i X_full, orthonormalise in the H_i inner product (twice) ----
+    launch_gather_rows(nW, S.w2p, vX, kp, 0, Xw, kp, 0, kp, st);
+    launch_gather_rows(nW, S.w2p, vX, kp, k, u0w, 1, 0, 1, st);
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_spmm<double>(S.tW, Hi.e64(), Xw, Yw, kp, st);
+      gram(S.tW, Xw, kp, k, Yw, kp, k, kp);
+      sym_eig(kp, k, evals, evecs);
+      launch_make_M(n_sd, 0, evals, evecs, kp, k, o.orth_tol, 0, Mm, kcnt, st);
+      rowmul(S.tW, Xw, kp, k, kp, Zw, kp, k);
+      std::swap(Xw, Zw);
+    }
+
+    // ---- adjoint: T = A_BI A_II^{-1} C_i^T H_i X^ (two left solves, the transposed form of Eq. (24)) ----
     launch_spmm<double>(S.tW, Hi.e64(), Xw, Yw, kp, st);
-    launch_gram(S.tW, n_sd, Xw, kp, k, Yw, kp, k, gpart, gcnt, G, kp, st);
-    launch_sym_eig(n_sd, G, kp, k, evals, evecs, st);
-    launch_make_M(n_sd, 0, evals, evecs, kp, k, o.orth_tol, 0, Mm, kcnt, st);
-    launch_rowmul(S.tW, Xw, kp, k, Mm, kp, Zw, kp, k, st);
-    std::swap(Xw, Zw);
+    CK(cudaMemsetAsync(vF, 0, nP * kp * sizeof(double), st));
+    launch_scatter_rows(nW, S.w2p, Yw, kp, vF, kp, kp, st);
+    TRY(solve(S.tP_I, A_II, true, vF, vX, k, 2, rt));
+    CK(cudaMemsetAsync(vS, 0, nP * kp * sizeof(double), st));
+    launch_spmm<double>(S.tP_B, A_BI.e64(), vX, vS, kp, st);
+    // S_B^{-1} T = ((H^+)^{-1} [0; T])_B  (Lemma 4.1 / block inverse of H^+)
+    TRY(solve(S.tP_all, Hp, false, vS, vG, k, 3, rt));
+    gram(S.tP_B, vS, kp, k, vG, kp, k, kp);
+    // eig(G_B) = sigma_j^2 (kept on the device as squares); the rotation of the top
+    // `rank` directions gives the basis X^ U_m = R_i^{-1} Qh U_m
+    sym_eig(kp, k, Bo.sigma, evecs);
+    // fixed rank: the first m_i directions; tolerance mode: sigma_j > eps (Eq. (15))
+    if (tol_mode)
+      launch_make_M(n_sd, 2, Bo.sigma, evecs, kp, k, o.eps * o.eps, k, Mm, d_msel, st, d_ksd);
+    else
+      launch_make_M(n_sd, 1, Bo.sigma, evecs, kp, k, 0.0, mcols, Mm, d_msel, st, d_msd);
+    TRY(finish_kq());
+    rowmul(S.tW, Xw, kp, k, kp, Zw, kp, mcols);
+    colsW = Zw;
   }
-
-  // ---- adjoint: T = A_BI A_II^{-1} C_i^T H_i X^ (two left solves, the transposed form of Eq. (24)) ----
-  launch_spmm<double>(S.tW, Hi.e64(), Xw, Yw, kp, st);
-  CK(cudaMemsetAsync(vF, 0, nP * kp * sizeof(double), st));
-  launch_scatter_rows(nW, S.w2p, Yw, kp, vF, kp, kp, st);
-  TRY(solve(S.tP_I, A_II, true, vF, vX, k, 2, rt));
-  CK(cudaMemsetAsync(vS, 0, nP * kp * sizeof(double), st));
-  launch_spmm<double>(S.tP_B, A_BI.e64(), vX, vS, kp, st);
-  // S_B^{-1} T = ((H^+)^{-1} [0; T])_B  (Lemma 4.1 / block inverse of H^+)
-  TRY(solve(S.tP_all, Hp, false, vS, vG, k, 3, rt));
-  launch_gram(S.tP_B, n_sd, vS, kp, k, vG, kp, k, gpart, gcnt, G, kp, st);
-  // eig(G_B) = sigma_j^2 (kept on the device as squares); the rotation of the top
-  // `rank` directions gives the basis X^ U_m = R_i^{-1} Qh U_m
-  launch_sym_eig(n_sd, G, kp, k, Bo.sigma, evecs, st);
-  // fixed rank: the first m_i directions; tolerance mode: sigma_j > eps (Eq. (15))
-  if (tol_mode)
-    launch_make_M(n_sd, 2, Bo.sigma, evecs, kp, k, o.eps * o.eps, mcols, Mm, d_msel, st, d_ksd);
-  else
-    launch_make_M(n_sd, 1, Bo.sigma, evecs, kp, k, 0.0, mcols, Mm, d_msel, st, d_msd);
-  launch_rowmul(S.tW, Xw, kp, k, Mm, kp, Zw, kp, mcols, st);
 
   // ---- V = D_i [u_0, X^ U_m], diagonal-block update Q_i = V W Lambda^{-1/2} ----
   launch_gather_rows(nO, S.o2w, u0w, 1, 0, V, kq, 0, 1, st);
-  launch_gather_rows(nO, S.o2w, Zw, kp, 0, V, kq, 1, mcols, st);
+  launch_gather_rows(nO, S.o2w, colsW, colsLd, 0, V, kq, 1, mcols, st);
   launch_spmm<double>(S.tO, App.e64(), V, AV, kq, st);
-  launch_gram(S.tO, n_sd, V, kq, mcols + 1, AV, kq, mcols + 1, gpart, gcnt, G, kq, st);
-  launch_sym_eig(n_sd, G, kq, mcols + 1, evals, evecs, st);
+  gram(S.tO, V, kq, mcols + 1, AV, kq, mcols + 1, kq);
+  sym_eig(kq, mcols + 1, evals, evecs);
   launch_make_M(n_sd, 0, evals, evecs, kq, mcols + 1, o.tau, 0, Mm, Bo.kept, st);
-  launch_rowmul(S.tO, V, kq, mcols + 1, Mm, kq, Bo.Q, kq, mcols + 1, st);
+  rowmul(S.tO, V, kq, mcols + 1, kq, Bo.Q, kq, mcols + 1);
   // b~_i = Q_i^T b[P_i]
   launch_gather_rows(nO, S.o2w, loadW, 1, 0, bP, 1, 0, 1, st);
   launch_gram_vec(S.tO, n_sd, Bo.Q, kq, kq, bP, 1, gpart, gcnt, Bo.bt, kq, st);
   CK(cudaGetLastError());
 
+  if (dense) {
+    // R_BB per subdomain for mor_bases_get_rbb
+    TRY(Bo.mem.alloc(&Bo.Rbb, (size_t)std::max<int64_t>(DW.h_bboff[n_sd], 1), false, st));
+    CK(cudaMemcpyAsync(Bo.Rbb, DW.Rbb, (size_t)DW.h_bboff[n_sd] * sizeof(double),
+                       cudaMemcpyDeviceToDevice, st));
+    Bo.rbb_off = DW.h_bboff;
+    Bo.rbb_m = DW.h_M;
+  }
   Bo.h_kept.resize(n_sd);
-  Bo.h_sigma.resize((size_t)n_sd * kp);
+  Bo.h_sigma.resize((size_t)n_sd * Bo.kp);
   CK(cudaMemcpyAsync(Bo.h_kept.data(), Bo.kept, n_sd * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(Bo.h_sigma.data(), Bo.sigma, (size_t)n_sd * kp * sizeof(double),
+  CK(cudaMemcpyAsync(Bo.h_sigma.data(), Bo.sigma, (size_t)n_sd * Bo.kp * sizeof(double),
                      cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   for (auto& s : Bo.h_sigma) s = std::sqrt(std::max(s, 0.0));
@@ -1013,6 +1409,9 @@ static int build_bases_streamed(const mor_subdomains* sd, const mor_basis_opts* 
   const HostPlan& g = sd->hp;
   const mor_basis_opts& o = *opts;
   cudaStream_t st = (cudaStream_t)stream;
+  const int sb = o.sub_begin, se = o.sub_end > 0 ? o.sub_end : g.n_sd;
+  if (sb < 0 || se > g.n_sd || sb >= se)
+    return fail(MOR_ERR_ARG, "mor_build_bases: bad subdomain range");
   int m_max = 0;
   for (int i = 0; i < g.n_sd; ++i) m_max = std::max(m_max, o.ranks ? o.ranks[i] : o.rank);
   auto bases = std::make_unique<mor_bases_s>();
@@ -1021,7 +1420,7 @@ static int build_bases_streamed(const mor_subdomains* sd, const mor_basis_opts* 
   int64_t not_conv = 0;
   // the host plan of the next wave is built while the device works on the current one
   auto plan_async = [&](int s0, HostPlan* out, std::string* err) {
-    const int s1 = std::min(g.n_sd, s0 + sd->wave_sd);
+    const int s1 = std::min(se, s0 + sd->wave_sd);
     return std::async(std::launch::async, [=, &g, &ps] {
       return build_wave_plan(g.n_nodes, g.n_tets, sd->h_tets.data(), sd->h_dir.data(),
                              sd->h_xyz.data(), g, s0, s1, *out, ps, *err);
@@ -1029,14 +1428,15 @@ static int build_bases_streamed(const mor_subdomains* sd, const mor_basis_opts* 
   };
   auto next_plan = std::make_unique<HostPlan>();
   std::string next_err;
-  std::future<int> next = plan_async(0, next_plan.get(), &next_err);
-  for (int s0 = 0; s0 < g.n_sd; s0 += sd->wave_sd) {
-    const int s1 = std::min(g.n_sd, s0 + sd->wave_sd), nw = s1 - s0;
+  std::future<int> next = plan_async(sb, next_plan.get(), &next_err);
+  bool first = true;
+  for (int s0 = sb; s0 < se; s0 += sd->wave_sd) {
+    const int s1 = std::min(se, s0 + sd->wave_sd), nw = s1 - s0;
     auto W = std::make_unique<mor_subdomains_s>();
     int rc = next.get();
     if (rc != MOR_OK) return fail(rc, next_err);
     W->hp = std::move(*next_plan);
-    if (s1 < g.n_sd) next = plan_async(s1, next_plan.get(), &next_err);
+    if (s1 < se) next = plan_async(s1, next_plan.get(), &next_err);
     // a return below leaves the pending plan to be joined by the future's destructor
     W->xyz = sd->xyz;
     W->tets = sd->tets;
@@ -1052,7 +1452,8 @@ static int build_bases_streamed(const mor_subdomains* sd, const mor_basis_opts* 
       not_conv += wb->stats[5];
     else if (rc != MOR_OK)
       return rc;
-    if (s0 == 0) {
+    if (first) {
+      first = false;
       Bo.n_sd = g.n_sd;
       Bo.k = wb->k;
       Bo.kp = wb->kp;
@@ -1092,6 +1493,8 @@ int mor_build_bases(const mor_subdomains* sd, const mor_basis_opts* opts, void* 
                     mor_bases** out) {
   if (!sd || !opts || !out) return fail(MOR_ERR_ARG, "mor_build_bases: null argument");
   if (sd->streamed) return build_bases_streamed(sd, opts, stream, out);
+  if (opts->sub_begin != 0 || (opts->sub_end > 0 && opts->sub_end != sd->hp.n_sd))
+    return fail(MOR_ERR_ARG, "mor_build_bases: a subdomain range needs a streamed plan");
   return build_bases_core(sd, opts, 0, stream, out);
 }
 
@@ -1120,6 +1523,17 @@ int mor_bases_get_Q(const mor_bases* h, int32_t sub, double* out) {
   if (!h || !out || sub < 0 || sub >= h->n_sd) return fail(MOR_ERR_ARG, "mor_bases_get_Q: bad argument");
   int64_t r0 = h->Ooff[sub], r1 = h->Ooff[sub + 1];
   CK(cudaMemcpy(out, h->Q + r0 * h->kq, (r1 - r0) * h->kq * sizeof(double),
+                cudaMemcpyDeviceToHost));
+  return MOR_OK;
+}
+
+int mor_bases_get_rbb(const mor_bases* h, int32_t sub, double* out) {
+  if (!h || !out || sub < 0 || sub >= h->n_sd)
+    return fail(MOR_ERR_ARG, "mor_bases_get_rbb: bad argument");
+  if (!h->Rbb)
+    return fail(MOR_ERR_STATE, "mor_bases_get_rbb: bases built without dense weights");
+  const int64_t m = h->rbb_m[sub];
+  CK(cudaMemcpy(out, h->Rbb + h->rbb_off[sub], (size_t)(m * m) * sizeof(double),
                 cudaMemcpyDeviceToHost));
   return MOR_OK;
 }
@@ -1212,18 +1626,34 @@ int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void*
   TRY(A.alloc(&s.counter, 1, true, st));
   TRY(A.alloc(&s.scal, 8, true, st));
   TRY(A.alloc(&s.flag, 2, true, st));
-  launch_rcg_init(h->n_sd, h->kq, h->bt, s, st);
   int hf[2] = {0, 0};
-  int it = 0;
-  while (it < max_iter) {
-    int chunk = std::min(16, max_iter - it);
-    for (int c = 0; c < chunk; ++c)
-      launch_rcg_step(h->n_sd, h->kq, h->nbr_ptr, h->nbr_sd, h->nbr_blk, h->blocks, rtol * rtol,
-                      s, st);
-    it += chunk;
+  unsigned* sync;
+  TRY(A.alloc(&sync, 4, true, st));
+  const int grid = launch_rcg_persistent(h->n_sd, h->kq, h->nbr_ptr, h->nbr_sd, h->nbr_blk,
+                                         h->blocks, h->bt, rtol * rtol, max_iter, s, sync,
+                                         wait_budget_cycles(), st);
+  if (grid > 0) {
+    unsigned hs[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(hs, sync, sizeof(hs), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hf, s.flag, sizeof(hf), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (hf[0]) break;
+    if (hs[2] != 0)
+      return fail(MOR_ERR_TIMEOUT, "mor_solve_reduced: a grid-barrier wait ran out of its "
+                                   "budget (mor_set_wait_budget)");
+  } else {
+    cudaGetLastError();  // no cooperative launch: three launches per step
+    launch_rcg_init(h->n_sd, h->kq, h->bt, s, st);
+    int it = 0;
+    while (it < max_iter) {
+      int chunk = std::min(16, max_iter - it);
+      for (int c = 0; c < chunk; ++c)
+        launch_rcg_step(h->n_sd, h->kq, h->nbr_ptr, h->nbr_sd, h->nbr_blk, h->blocks,
+                        rtol * rtol, s, st);
+      it += chunk;
+      CK(cudaMemcpyAsync(hf, s.flag, sizeof(hf), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (hf[0]) break;
+    }
   }
   CK(cudaGetLastError());
   double sc[8];
@@ -1242,6 +1672,33 @@ int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void*
   }
   if (!(hf[0] && sc[4] <= rtol * rtol * sc[1]))
     return fail(MOR_ERR_NOT_CONVERGED, "mor_solve_reduced: max_iter reached");
+  return MOR_OK;
+}
+
+int mor_set_wait_budget(double seconds) {
+  if (!(seconds >= 0.0) || seconds > 3600.0)
+    return fail(MOR_ERR_ARG, "mor_set_wait_budget: seconds must lie in [0, 3600]");
+  g_wait_budget_s = seconds;
+  return MOR_OK;
+}
+
+int mor_debug_wait_timeout(double seconds, int32_t* timed_out) {
+  if (!timed_out || !(seconds >= 0.0) || seconds > 10.0)
+    return fail(MOR_ERR_ARG, "mor_debug_wait_timeout: bad argument");
+  Allocs A;
+  unsigned* sync;
+  int* status;
+  TRY(A.alloc(&sync, 4, true));
+  TRY(A.alloc(&status, 1, true));
+  const double keep = g_wait_budget_s;
+  g_wait_budget_s = seconds;
+  const long long cycles = wait_budget_cycles();
+  g_wait_budget_s = keep;
+  launch_wait_unset_flag(sync, cycles, status, nullptr);
+  int h = -1;
+  CK(cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost));
+  *timed_out = h == 1 ? 1 : 0;
+  if (h == 1) return fail(MOR_ERR_TIMEOUT, "mor_debug_wait_timeout: the wait ran out");
   return MOR_OK;
 }
 

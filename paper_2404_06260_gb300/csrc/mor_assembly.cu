@@ -111,7 +111,8 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
   hi = s;
 }
 
-// one warp per row, lanes over columns: out[r, j] = sum over incident elements T of
+// one thread per (row, column), consecutive threads taking consecutive columns of a
+// row: out[r, j] = sum over incident elements T of
 // (L_T xi_T[:, j])[a(r)].  The Gaussian draws are binary32 (bit-exact Box-Muller); the
 // products and sums run in double-binary32 arithmetic (about 2^-48 relative), the same in
 // every solve precision, so every precision sketches with the same test matrix W

@@ -198,15 +198,18 @@ __global__ void k_make_M(int mode, const double* __restrict__ evals,
   double* Ms = M + (int64_t)sd * ld * ld;
   double l0 = ev[0];
   const int kmax = keep_sd ? min(keep, (int)keep_sd[sd]) : keep;
+  // mode 0: eigenvalues above rel * largest; 1: the first kmax; 2: the first kmax above
+  // rel; 3 and 4: as 1 and 2; modes 0, 3 and 4 scale column j by ev[j]^(-1/2)
   auto take = [&](int j) -> bool {
     if (mode == 0) return l0 > 0.0 && ev[j] > rel * l0;
-    if (mode == 1) return j < kmax;
+    if (mode == 1 || mode == 3) return j < kmax && (mode == 1 || ev[j] > 0.0);
     return j < kmax && ev[j] > rel;
   };
+  const bool scaled = mode == 0 || mode >= 3;
   for (int idx = threadIdx.x; idx < ld * ld; idx += blockDim.x) {
     int l = idx / ld, j = idx % ld;
     double val = 0.0;
-    if (l < n && j < n && take(j)) val = (mode == 0) ? V[l * ld + j] / sqrt(ev[j]) : V[l * ld + j];
+    if (l < n && j < n && take(j)) val = scaled ? V[l * ld + j] / sqrt(ev[j]) : V[l * ld + j];
     Ms[idx] = val;
   }
   if (threadIdx.x == 0 && kept) {

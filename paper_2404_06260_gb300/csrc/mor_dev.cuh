@@ -155,4 +155,48 @@ __device__ __forceinline__ void field_normals(uint32_t T, uint32_t j, uint32_t i
   box_muller(c[2], c[3], z[2], z[3]);
 }
 
+// Bounded wait of one thread until *gen differs from `seen` (a grid barrier's
+// generation counter, or any flag another block or the host sets).  It gives up after
+// `budget` clock cycles, or as soon as *err is non-zero (another block gave up), sets
+// *err to 1 when it is the one that ran out, and returns false; true when the flag
+// moved.  The caller's block then leaves its kernel, so no wait is unbounded.
+__device__ __forceinline__ bool bounded_wait(const volatile unsigned* gen, unsigned seen,
+                                             volatile int* err, long long budget) {
+  const long long t0 = clock64();
+  while (*gen == seen) {
+    if (*err) return false;
+    if (clock64() - t0 > budget) {
+      atomicExch((int*)err, 1);
+      return false;
+    }
+    __nanosleep(100);
+  }
+  return true;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident) with bounded
+// waits: arrivals count on *count; the last one resets it and advances *gen.  Returns
+// false (for every thread of the block) when the block gave up waiting.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, volatile unsigned* gen,
+                                             volatile int* err, long long budget) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned seen = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd((unsigned*)gen, 1u);
+      ok = 1;
+    } else {
+      ok = bounded_wait(gen, seen, err, budget) ? 1 : 0;
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 }  // namespace mor

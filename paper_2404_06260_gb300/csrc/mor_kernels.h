@@ -231,6 +231,41 @@ void launch_make_M(int n_sd, int mode, const double* evals, const double* evecs,
 void launch_rowmul(const DTiles& tiles, const double* X, int ldx, int nin, const double* M,
                    int ldm, double* Y, int ldy, int nout, cudaStream_t st);
 // dst[r, dc0 + c] = src[map[r], sc0 + c] (map null: r), c < ncols
+// wide-sketch versions (k up to 511 columns, mor_wide.cu): the Gram needs a partial
+// buffer of n_sd * gram_wide_chunks(n_sd, nx, ny) * nx * ny doubles, the eigensolver a
+// work buffer of n_sd * 2 * m * m doubles (m = n rounded up to even, n <= 1024)
+int gram_wide_chunks(int n_sd, int nx, int ny);
+void launch_gram_wide(const DTiles& tiles, int n_sd, const double* X, int ldx, int nx,
+                      const double* Y, int ldy, int ny, double* part, double* G, int ldg,
+                      int64_t sd_stride, cudaStream_t st);
+void launch_sym_eig_wide(int n_sd, const double* A, int ld, int n, double* evals,
+                         double* evecs, double* work, cudaStream_t st);
+void launch_rowmul_wide(const DTiles& tiles, const double* X, int ldx, int nin,
+                        const double* M, int ldm, double* Y, int ldy, int nout,
+                        cudaStream_t st);
+// paper-literal weights (mor_explicit.cu): dense per-subdomain factors
+void launch_ell_to_dense(int64_t n_rows, const int32_t* row_sd, const int32_t* rloc,
+                         const int32_t* cloc, const EllView<double>& A, const int32_t* r_sub,
+                         const int32_t* r_n, const int32_t* c_sub, const int32_t* ncols,
+                         const int32_t* ld, const int64_t* doff, double* D, cudaStream_t st);
+void launch_potrf(int n_sd, int n_max, double* D, const int64_t* doff, const int32_t* nn,
+                  int* bad, cudaStream_t st);
+void launch_transpose_block(int n_sd, int m_max, const double* In, const int64_t* ioff,
+                            const int32_t* nn, const int32_t* soff, const int32_t* mm,
+                            double* Out, const int64_t* ooff, int transpose, cudaStream_t st);
+void launch_trsv_cols(int n_sd, int n_max, int ncol_max, const double* T, const int64_t* toff,
+                      const int32_t* nn, const int32_t* tld, const int32_t* tsh, double* X,
+                      const int64_t* roff, int ldx, const int32_t* ncol, int forward,
+                      cudaStream_t st);
+void launch_trsv_rows(const double* R, const int64_t* roff_r, const int32_t* mm, double* X,
+                      const int64_t* roff, int ldx, const int* sd_of_warp,
+                      const int* row_of_warp, int n_warps, cudaStream_t st);
+void launch_trmv_upper(int n_sd, int n_max, int ncol_max, const double* U, const int64_t* uoff,
+                       const int32_t* nn, const double* Z, double* Y, const int64_t* roff,
+                       int ld, const int32_t* ncol, cudaStream_t st);
+void launch_node_normals(int n_sd, int m_max, const int32_t* bnode, const int64_t* boff,
+                         const int32_t* mm, const int32_t* kk, int k, uint64_t seed,
+                         uint32_t sd_base, double* out, int ld, cudaStream_t st);
 void launch_gather_rows(int64_t n_rows, const int32_t* map, const double* src, int lds,
                         int sc0, double* dst, int ldd, int dc0, int ncols, cudaStream_t st);
 // dst[map[r], c] = src[r, c]
@@ -253,6 +288,13 @@ struct RcgState {
   double* scal;             // [0] rz, [1] bb, [2] alpha, [3] beta, [4] rr
   int* flag;                // [0] done, [1] iterations
 };
+// the reduced CG in one cooperative launch with bounded grid-barrier waits; returns the
+// grid size, or -1 when a cooperative launch is not possible.  sync: 3 zeroed words.
+int launch_rcg_persistent(int n_sd, int kq, const int32_t* nbr_ptr, const int32_t* nbr_sd,
+                          const int32_t* nbr_blk, const double* blocks, const double* bt,
+                          double tol2, int max_iter, const RcgState& s, unsigned* sync,
+                          long long budget, cudaStream_t st);
+void launch_wait_unset_flag(unsigned* sync, long long budget, int* status, cudaStream_t st);
 void launch_rcg_init(int n_sd, int kq, const double* bt, const RcgState& s,
                      cudaStream_t st);
 void launch_rcg_step(int n_sd, int kq, const int32_t* nbr_ptr, const int32_t* nbr_sd,

@@ -1,6 +1,7 @@
 // The reduced solve of mor_solve_reduced in a form that allocates nothing: its work
 // vectors live in one fixed device array of this file instead of cudaMalloc'd buffers.
 // It runs the same CG kernels (mor_reduced.cu) on caller-owned inputs and output.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -16,8 +17,10 @@ namespace {
 
 // Limits of the fixed scratch array: the reduced vectors r, p, q (3 x kMaxDim binary64),
 // the per-subdomain partial sums (2 x kMaxSub), 8 scalars and a 3-int tail (ticket
-// counter, done flag, iteration count).  About 12.5 MB, held by every GPU that loads
-// the library until the process exits.
+// counter, done flag, iteration count): 1,703,952 doubles = 13.6 MB.  The array is
+// placed on a device when this file's device code is loaded there (with CUDA's default
+// lazy loading: at the first set-up below on that device) and stays until the process
+// exits.
 constexpr int64_t kMaxDim = int64_t(1) << 19;  // 524,288 reduced unknowns
 constexpr int64_t kMaxSub = int64_t(1) << 16;  // 65,536 subdomains
 constexpr int64_t kVecOff = 0;
@@ -25,30 +28,71 @@ constexpr int64_t kPartOff = 3 * kMaxDim;
 constexpr int64_t kScalOff = kPartOff + 2 * kMaxSub;
 constexpr int64_t kIntOff = kScalOff + 8;
 constexpr int64_t kScratchDoubles = kIntOff + 8;
+static_assert(kScratchDoubles == 1703952, "stated scratch size");
 
 static __device__ __align__(256) double g_solve_scratch[kScratchDoubles];
 
-// Host-side address of g_solve_scratch per device.  In host code the symbol itself is a
-// host stand-in, not a device address, so the address is looked up once per device
-// (with that device current) and cached.
+// Device address of g_solve_scratch.  In host code the symbol is a host stand-in, not a
+// device address, so the set-up looks the address up with cudaGetSymbolAddress, once per
+// device and CUDA context, with that device current.  The cache is keyed by the
+// context's unique id: after cudaDeviceReset the device gets a new context, the module
+// is loaded again (possibly elsewhere) and the address is looked up again.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
 std::mutex g_mu;
 constexpr int kMaxDevices = 128;
-double* g_dev_ptr[kMaxDevices] = {};
+struct Slot {
+  unsigned long long ctx_id = 0;
+  double* ptr = nullptr;
+};
+Slot g_slot[kMaxDevices];
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+int driver_fns() {
+  if (g_ctx_current && g_ctx_id) return MOR_OK;
+  void* f1 = nullptr;
+  void* f2 = nullptr;
+  cudaDriverEntryPointQueryResult q1, q2;
+  cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                    cudaEnableDefault, &q1);
+  cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000,
+                                                    cudaEnableDefault, &q2);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || q1 != cudaDriverEntryPointSuccess ||
+      q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+    return set_error(MOR_ERR_CUDA, "mor_solve_reduced_noalloc: driver context query unavailable");
+  g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+  g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+  return MOR_OK;
+}
 
 int scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(MOR_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return set_error(MOR_ERR_ARG, "mor_solve_reduced_noalloc: device index out of range");
+  // cudaSetDevice initialises the device's primary context and makes it current (a
+  // no-op when it already is)
+  e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return set_error(MOR_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_ptr[dev]) {
+  int rc = driver_fns();
+  if (rc != MOR_OK) return rc;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_id(ctx, &id) != CUDA_SUCCESS)
+    return set_error(MOR_ERR_CUDA, "mor_solve_reduced_noalloc: no current CUDA context");
+  Slot& s = g_slot[dev];
+  if (!s.ptr || s.ctx_id != id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_solve_scratch);
     if (e != cudaSuccess || !p)
       return set_error(MOR_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_dev_ptr[dev] = static_cast<double*>(p);
+    s.ptr = static_cast<double*>(p);
+    s.ctx_id = id;
   }
-  *out = g_dev_ptr[dev];
+  *out = s.ptr;
   return MOR_OK;
 }
 

@@ -2,13 +2,16 @@
 // interface couplings of neighbouring subdomains, the reduced CG solve (diagonal
 // preconditioner = identity because every diagonal block is I after the step-2
 // update), and the lift u~ = sum_i S_i Q_i x_i.
+#include "mor_dev.cuh"
 #include "mor_kernels.h"
+
+#include <algorithm>
 
 namespace mor {
 namespace {
 
 constexpr int kPairThreads = 512;
-constexpr int kPairPerThread = 13;  // 512 * 13 >= 80 * 80
+constexpr int kPairPerThread = 32;  // 512 * 32 >= 128 * 128
 constexpr int kPairChunk = 32;
 
 __global__ void __launch_bounds__(kPairThreads)
@@ -184,6 +187,109 @@ __global__ void k_rcg_update_p(int kq, RcgState s) {
   }
 }
 
+// The whole reduced CG in one cooperative launch: blocks take block rows sd =
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the three phases of an iteration (q = K~ p
+// with p.q; x and r update with r.r; p update) are separated by grid barriers with
+// bounded waits.  Every block forms the scalars itself from the same partial sums in
+// the same order (sum_parts), so all blocks take the same decisions; the arithmetic is
+// that of the three-kernel iteration.  sync[0] barrier count, sync[1] generation,
+// sync[2] error (a wait ran out).
+__global__ void __launch_bounds__(128)
+    k_rcg_persistent(int n_sd, int kq, const int32_t* __restrict__ nbr_ptr,
+                     const int32_t* __restrict__ nbr_sd, const int32_t* __restrict__ nbr_blk,
+                     const double* __restrict__ blocks, const double* __restrict__ bt,
+                     double tol2, int max_iter, RcgState s, unsigned* sync,
+                     long long budget) {
+  __shared__ double red[128];
+  unsigned* count = sync;
+  volatile unsigned* gen = sync + 1;
+  volatile int* err = reinterpret_cast<volatile int*>(sync + 2);
+  // x = 0, r = p = b~, ||b~||^2
+  for (int sd = blockIdx.x; sd < n_sd; sd += gridDim.x) {
+    double loc = 0.0;
+    for (int i = threadIdx.x; i < kq; i += blockDim.x) {
+      const int64_t g = (int64_t)sd * kq + i;
+      const double b = bt[g];
+      s.x[g] = 0.0;
+      s.r[g] = b;
+      s.p[g] = b;
+      loc += b * b;
+    }
+    const double t = block_sum128(loc, red);
+    if (threadIdx.x == 0) s.part[2 * sd] = t;
+  }
+  if (!grid_barrier(count, gen, err, budget)) return;
+  const double bb = sum_parts(s.part, n_sd, 2, 0, red);
+  double rz = bb, rr = bb;
+  int done = bb > 0.0 ? 0 : 1, it = 0;
+  while (!done && it < max_iter) {
+    // q = K~ p (identity diagonal blocks) and p.q
+    for (int sd = blockIdx.x; sd < n_sd; sd += gridDim.x) {
+      double loc = 0.0;
+      for (int i = threadIdx.x; i < kq; i += blockDim.x) {
+        const int64_t g = (int64_t)sd * kq + i;
+        double acc = s.p[g];
+        for (int q = nbr_ptr[sd]; q < nbr_ptr[sd + 1]; ++q) {
+          const double* B = blocks + (int64_t)nbr_blk[q] * kq * kq + (int64_t)i * kq;
+          const double* pj = s.p + (int64_t)nbr_sd[q] * kq;
+          for (int l = 0; l < kq; ++l) acc += B[l] * pj[l];
+        }
+        s.q[g] = acc;
+        loc += s.p[g] * acc;
+      }
+      const double t = block_sum128(loc, red);
+      if (threadIdx.x == 0) s.part[2 * sd] = t;
+    }
+    if (!grid_barrier(count, gen, err, budget)) return;
+    const double pq = sum_parts(s.part, n_sd, 2, 0, red);
+    const double al = pq > 0.0 ? rz / pq : 0.0;
+    for (int sd = blockIdx.x; sd < n_sd; sd += gridDim.x) {
+      double loc = 0.0;
+      for (int i = threadIdx.x; i < kq; i += blockDim.x) {
+        const int64_t g = (int64_t)sd * kq + i;
+        s.x[g] += al * s.p[g];
+        const double r = s.r[g] - al * s.q[g];
+        s.r[g] = r;
+        loc += r * r;
+      }
+      const double t = block_sum128(loc, red);
+      if (threadIdx.x == 0) s.part[2 * sd + 1] = t;
+    }
+    if (!grid_barrier(count, gen, err, budget)) return;
+    rr = sum_parts(s.part, n_sd, 2, 1, red);
+    ++it;
+    double be = 0.0;
+    if (rr <= tol2 * bb || !(rz > 0.0)) {
+      done = 1;
+    } else {
+      be = rr / rz;
+      rz = rr;
+    }
+    if (!done) {
+      for (int sd = blockIdx.x; sd < n_sd; sd += gridDim.x)
+        for (int i = threadIdx.x; i < kq; i += blockDim.x) {
+          const int64_t g = (int64_t)sd * kq + i;
+          s.p[g] = s.r[g] + be * s.p[g];
+        }
+      if (!grid_barrier(count, gen, err, budget)) return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s.scal[0] = rz;
+    s.scal[1] = bb;
+    s.scal[4] = rr;
+    s.flag[0] = done;
+    s.flag[1] = it;
+  }
+}
+
+// a bounded wait on a flag that nothing sets (the timeout path of the grid barrier)
+__global__ void k_wait_unset_flag(unsigned* sync, long long budget, int* status) {
+  volatile unsigned* gen = sync + 1;
+  volatile int* err = reinterpret_cast<volatile int*>(sync + 2);
+  if (threadIdx.x == 0) *status = bounded_wait(gen, *gen, err, budget) ? 0 : 1;
+}
+
 __global__ void k_lift(int64_t n_o, const int32_t* __restrict__ o_node,
                        const int32_t* __restrict__ o_sd, const double* __restrict__ Q, int kq,
                        const double* __restrict__ x, double* u) {
@@ -202,6 +308,12 @@ void launch_pair_blocks(int n_pairs, const int64_t* pair_ptr, const int32_t* uro
                         double* blocks, cudaStream_t st) {
   if (n_pairs <= 0) return;
   size_t sm = sizeof(double) * (2 * (size_t)kPairChunk * kq + kPairChunk);
+  static bool attr = false;
+  if (!attr) {  // kq up to 128: 66 KB
+    cudaFuncSetAttribute(k_pair_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         100 * 1024);
+    attr = true;
+  }
   count_launch();
   k_pair_blocks<<<n_pairs, kPairThreads, sm, st>>>(pair_ptr, urow, vrow, aval, Q, kq, blocks);
 }
@@ -221,6 +333,35 @@ void launch_rcg_step(int n_sd, int kq, const int32_t* nbr_ptr, const int32_t* nb
   k_rcg_update_xr<<<n_sd, 128, 0, st>>>(n_sd, kq, tol2, s);
   count_launch();
   k_rcg_update_p<<<n_sd, 128, 0, st>>>(kq, s);
+}
+
+int launch_rcg_persistent(int n_sd, int kq, const int32_t* nbr_ptr, const int32_t* nbr_sd,
+                          const int32_t* nbr_blk, const double* blocks, const double* bt,
+                          double tol2, int max_iter, const RcgState& s, unsigned* sync,
+                          long long budget, cudaStream_t st) {
+  int dev = 0, nsm = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rcg_persistent, 128, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return -1;
+  int grid = std::min(n_sd, nsm * per_sm);
+  RcgState sc = s;
+  void* args[] = {&n_sd, &kq, (void*)&nbr_ptr, (void*)&nbr_sd, (void*)&nbr_blk,
+                  (void*)&blocks, (void*)&bt, &tol2, &max_iter, &sc, &sync, &budget};
+  count_launch();
+  if (cudaLaunchCooperativeKernel((const void*)k_rcg_persistent, grid, 128, args, 0, st) !=
+      cudaSuccess)
+    return -1;
+  return grid;
+}
+
+void launch_wait_unset_flag(unsigned* sync, long long budget, int* status, cudaStream_t st) {
+  count_launch();
+  k_wait_unset_flag<<<1, 32, 0, st>>>(sync, budget, status);
 }
 
 void launch_lift(int64_t n_o, const int32_t* o_node, const int32_t* o_sd, const double* Q,

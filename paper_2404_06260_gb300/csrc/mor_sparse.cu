@@ -114,25 +114,28 @@ __device__ __forceinline__ bool last_block(const Geo& g, int* counter, int sd, i
   return is_last;
 }
 
-// sums[c] = sum over tiles lo..hi-1 of part[t*kp + c], fixed order
+// sums[c] = sum over tiles lo..hi-1 of part[t*kp + c], fixed order.  Columns are taken
+// in groups of at most nth; within a group S = nth / group threads share a column.
 __device__ void sd_colsums(const Geo& g, const double* part, int kp, int lo, int hi,
                            double* scratch, double* sums) {
-  int S = g.nth / kp;
-  if (S < 1) S = 1;
-  int c = g.tid % kp, sidx = g.tid / kp;
-  double acc = 0.0;
-  if (sidx < S) {
+  for (int c0 = 0; c0 < kp; c0 += g.nth) {
+    const int cw = min(kp - c0, g.nth);
+    const int S = g.nth / cw;
+    const int c = c0 + g.tid % cw, sidx = g.tid / cw;
+    double acc = 0.0;
+    if (sidx < S) {
 #pragma unroll 4
-    for (int t = lo + sidx; t < hi; t += S) acc += __ldcg(part + (int64_t)t * kp + c);
+      for (int t = lo + sidx; t < hi; t += S) acc += __ldcg(part + (int64_t)t * kp + c);
+    }
+    scratch[g.tid] = acc;
+    __syncthreads();
+    for (int cc = g.tid; cc < cw; cc += g.nth) {
+      double s = 0.0;
+      for (int q = 0; q < S; ++q) s += scratch[q * cw + cc];
+      sums[c0 + cc] = s;
+    }
+    __syncthreads();
   }
-  scratch[g.tid] = acc;
-  __syncthreads();
-  for (int cc = g.tid; cc < kp; cc += g.nth) {
-    double s = 0.0;
-    for (int q = 0; q < S; ++q) s += scratch[q * kp + cc];
-    sums[cc] = s;
-  }
-  __syncthreads();
 }
 
 // CG coefficients: binary64 state with a binary32 copy

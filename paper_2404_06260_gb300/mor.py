@@ -14,6 +14,7 @@ from ._build import LIB
 
 MOR_OK = 0
 MOR_ERR_NOT_CONVERGED = -4
+MOR_ERR_TIMEOUT = -5
 FP64 = 0
 MIXED = 1
 
@@ -33,6 +34,11 @@ class _MeshC(ctypes.Structure):
                 ("xyz_dev", _P), ("tets_dev", _P), ("kappa_dev", _P)]
 
 
+class _MeshHostC(ctypes.Structure):
+    _fields_ = [("n_nodes", _i64), ("n_tets", _i64), ("tets", _P), ("dirichlet", _P),
+                ("xyz", _P), ("kappa", _P)]
+
+
 class BasisOpts(ctypes.Structure):
     _fields_ = [("rank", _i32), ("oversample", _i32), ("ranks", _P), ("eps", _dbl),
                 ("seed", ctypes.c_uint64),
@@ -40,7 +46,9 @@ class BasisOpts(ctypes.Structure):
                 ("max_iter", _i32), ("replace_every", _i32), ("normwise", _i32),
                 ("drift_restart", _dbl),
                 ("sketch_rtol", _dbl), ("tau", _dbl), ("orth_tol", _dbl),
-                ("coarse_rows", _i32), ("h1_weighted", _i32)]
+                ("coarse_rows", _i32), ("h1_weighted", _i32), ("sketch_div", _i32),
+                ("sub_begin", _i32),
+                ("sub_end", _i32), ("explicit_svd", _i32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -56,6 +64,8 @@ def _sig(name, res, *args):
 
 
 _sig("mor_build_subdomains", _i32, ctypes.POINTER(_MeshC), _P, _i32, _P, ctypes.POINTER(_P))
+_sig("mor_build_subdomains_host", _i32, ctypes.POINTER(_MeshHostC), _P, _i32, _i32, _P,
+     ctypes.POINTER(_P))
 _sig("mor_build_subdomains_streamed", _i32, ctypes.POINTER(_MeshC), _P, _i32, _i32, _P,
      ctypes.POINTER(_P))
 _sig("mor_debug_plan_check", _i32, _i64, _i64, _P, _P, _P, _P, _i32, _i32, _i32, _P)
@@ -67,6 +77,7 @@ _sig("mor_bases_info", _i32, _P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P,
      ctypes.POINTER(_i64))
 _sig("mor_bases_sigma", _i32, _P, _P)
 _sig("mor_bases_get_Q", _i32, _P, _i32, _P)
+_sig("mor_bases_get_rbb", _i32, _P, _i32, _P)
 _sig("mor_bases_get_bt", _i32, _P, _P)
 _sig("mor_bases_stats", _i32, _P, _P)
 _sig("mor_project", _i32, _P, _P, _P, ctypes.POINTER(_P))
@@ -76,6 +87,8 @@ _sig("mor_solve_reduced", _i32, _P, _dbl, _i32, _P, _P, ctypes.POINTER(SolveInfo
 _sig("mor_solve_reduced_noalloc", _i32, _i32, _i32, _P, _P, _P, _P, _P, _dbl, _i32, _P, _P,
      ctypes.POINTER(SolveInfo))
 _sig("mor_lift", _i32, _P, _P, _P, _P, _P)
+_sig("mor_set_wait_budget", _i32, _dbl)
+_sig("mor_debug_wait_timeout", _i32, _dbl, ctypes.POINTER(_i32))
 _sig("mor_energy_norm", _i32, _P, _P, _P, ctypes.POINTER(_dbl), _P)
 _sig("mor_debug_sketch_rhs", _i32, _P, ctypes.POINTER(BasisOpts), _i32, _P, _P)
 _sig("mor_profile_enable", _i32, _i32)
@@ -87,12 +100,14 @@ _sig("mor_free_bases", None, _P)
 _sig("mor_free_reduced", None, _P)
 _sig("mor_last_error", ctypes.c_char_p)
 
-EXPORTED = ["mor_build_subdomains", "mor_build_subdomains_streamed", "mor_subdomains_counts",
+EXPORTED = ["mor_build_subdomains", "mor_build_subdomains_host",
+            "mor_build_subdomains_streamed", "mor_subdomains_counts",
             "mor_subdomains_indices",
             "mor_basis_opts_default", "mor_build_bases", "mor_bases_info", "mor_bases_sigma",
-            "mor_bases_get_Q", "mor_bases_get_bt", "mor_bases_stats", "mor_project",
+            "mor_bases_get_Q", "mor_bases_get_rbb", "mor_bases_get_bt", "mor_bases_stats", "mor_project",
             "mor_reduced_info", "mor_reduced_dense", "mor_solve_reduced",
-            "mor_solve_reduced_noalloc", "mor_lift",
+            "mor_solve_reduced_noalloc", "mor_set_wait_budget", "mor_debug_wait_timeout",
+            "mor_lift",
             "mor_energy_norm", "mor_debug_sketch_rhs", "mor_debug_plan_check",
             "mor_profile_enable",
             "mor_profile_reset", "mor_profile_query", "mor_kernel_launches", "mor_free_subdomains",
@@ -151,6 +166,13 @@ class Mesh:
                       _P(self.kappa_d.data_ptr()))
 
 
+class _HostMeshInfo:
+    """Sizes of a mesh whose device copies belong to the library's handle."""
+
+    def __init__(self, n_nodes, n_tets):
+        self.n_nodes, self.n_tets = n_nodes, n_tets
+
+
 class Subdomains:
     """Step 1.  wave > 0 builds a streamed plan (mor_build_subdomains_streamed):
     mor_build_bases then works in waves of `wave` subdomains."""
@@ -175,6 +197,43 @@ class Subdomains:
         self.counts = np.zeros((self.n_sub, 7), dtype=np.int64)
         _check(_lib.mor_subdomains_counts(h, None, _ptr(self.counts)))
 
+    @classmethod
+    def from_host(cls, xyz, tets, kappa, dirichlet, owner, r_hops: int, stream=None,
+                  wave: int = 0):
+        """Step 1 from host arrays (mor_build_subdomains_host): the library copies the
+        mesh to the device itself; numpy arrays or (pinned) CPU tensors."""
+        self = cls.__new__(cls)
+        arrs = []
+
+        def host(a, dt):
+            if isinstance(a, torch.Tensor):
+                assert a.device.type == "cpu" and a.is_contiguous() and a.dtype == dt[1]
+                arrs.append(a)
+                return _P(a.data_ptr()), int(a.shape[0])
+            a = np.ascontiguousarray(a, dtype=dt[0])
+            arrs.append(a)
+            return a.ctypes.data_as(_P), int(a.shape[0])
+
+        px, nn = host(xyz, (np.float64, torch.float64))
+        pt, nt = host(tets, (np.int32, torch.int32))
+        pk, _ = host(kappa, (np.float64, torch.float64))
+        pd, _ = host(dirichlet, (np.uint8, torch.uint8))
+        self._owner = np.ascontiguousarray(owner, dtype=np.int32)
+        self.mesh = _HostMeshInfo(nn, nt)
+        self.streamed = wave > 0
+        h = _P()
+        mc = _MeshHostC(nn, nt, pt, pd, px, pk)
+        _check(_lib.mor_build_subdomains_host(ctypes.byref(mc), _ptr(self._owner),
+                                              int(r_hops), int(wave), _stream(stream),
+                                              ctypes.byref(h)))
+        self.h = h
+        n = _i32()
+        _check(_lib.mor_subdomains_counts(h, ctypes.byref(n), None))
+        self.n_sub = n.value
+        self.counts = np.zeros((self.n_sub, 7), dtype=np.int64)
+        _check(_lib.mor_subdomains_counts(h, None, _ptr(self.counts)))
+        return self
+
     def indices(self, sub: int, which: int) -> np.ndarray:
         # streamed plans keep no index sets (count -1): the library answers MOR_ERR_STATE
         n = int(self.counts[sub, which])
@@ -196,6 +255,8 @@ def basis_opts(**kw) -> BasisOpts:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": FP64, "mixed": MIXED}[v]
+        if k == "sketch" and isinstance(v, str):
+            v = {"field": 0, "paper": 1}[v]
         if k == "ranks":
             arr = np.ascontiguousarray(v, dtype=np.int32)
             o._ranks = arr
@@ -228,6 +289,12 @@ class Bases:
     def Q(self, sub: int) -> np.ndarray:
         out = np.zeros((int(self.sd.counts[sub, 3]), self.kq))
         _check(_lib.mor_bases_get_Q(self.h, int(sub), _ptr(out)))
+        return out
+
+    def rbb(self, sub: int) -> np.ndarray:
+        m = int(self.sd.counts[sub, 1])
+        out = np.zeros((m, m))
+        _check(_lib.mor_bases_get_rbb(self.h, int(sub), _ptr(out)))
         return out
 
     def bt(self) -> np.ndarray:
@@ -276,6 +343,19 @@ class Reduced:
         if getattr(self, "h", None):
             _lib.mor_free_reduced(self.h)
             self.h = None
+
+
+def set_wait_budget(seconds: float):
+    _check(_lib.mor_set_wait_budget(float(seconds)))
+
+
+def debug_wait_timeout(seconds: float) -> bool:
+    """True when a bounded wait on a flag nothing sets ran out and returned."""
+    t = _i32()
+    rc = _lib.mor_debug_wait_timeout(float(seconds), ctypes.byref(t))
+    if rc not in (MOR_OK, MOR_ERR_TIMEOUT):
+        _check(rc)
+    return bool(t.value)
 
 
 def lift(sd: Subdomains, bases: Bases, x, stream=None):

@@ -15,6 +15,8 @@ from .meshes import (  # noqa: F401
     box_owner,
     slab_owner,
     kmeans_owner,
+    kuhn_box_tets,
+    box_node_range,
     workload,
     WORKLOADS,
 )

@@ -97,6 +97,25 @@ def kuhn_cube(n: int, jitter: float = 0.0, seed: int = 0) -> Mesh:
                 dirichlet=dirichlet)
 
 
+def kuhn_box_tets(n: int, lo, hi) -> np.ndarray:
+    """Ids of the tetrahedra of kuhn_cube(n) in the cells lo <= (cx, cy, cz) < hi
+    (clipped to the cube): cell (cx, cy, cz) holds tetrahedra 6 c .. 6 c + 5 with
+    c = cx + n (cy + n cz)."""
+    lo = [max(0, int(v)) for v in lo]
+    hi = [min(n, int(v)) for v in hi]
+    cz, cy, cx = np.meshgrid(np.arange(lo[2], hi[2]), np.arange(lo[1], hi[1]),
+                             np.arange(lo[0], hi[0]), indexing="ij")
+    c = (cx + n * (cy + n * cz)).ravel().astype(np.int64)
+    return (6 * c[:, None] + np.arange(6)[None, :]).ravel()
+
+
+def box_node_range(n: int, parts: int, a: int):
+    """Node index range [lo, hi) along one axis owned by box a of box_owner(n, parts)."""
+    i = np.arange(n + 1)
+    own = np.flatnonzero(np.minimum(parts - 1, (i * parts) // n) == a)
+    return int(own[0]), int(own[-1]) + 1
+
+
 def lognormal_kappa(n_tets: int, seed: int) -> np.ndarray:
     """k_T = exp(g_T), g_T iid N(0,1) per element."""
     rng = np.random.default_rng(seed)

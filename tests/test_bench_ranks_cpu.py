@@ -62,3 +62,19 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = argparse.Namespace(workload="cube64_p4", steps=3, warmup=3, gpus=2)
     assert bench.reference_arm(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_times_the_oracle_over_a_process_pool(capsys):
+    # one single-threaded spawn worker per core over the smallest subdomains, one JSON
+    # line with the cores the pool used
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.pop("RANK", None)
+    os.environ.pop("WORLD_SIZE", None)
+    args = argparse.Namespace(workload="cube16_p2", steps=1, warmup=0, gpus=1)
+    assert bench.reference_arm(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == min(os.cpu_count(), 8)
+    assert line["config"]["subdomains"] == line["cpu_baseline"]["cores"]

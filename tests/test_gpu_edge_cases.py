@@ -7,8 +7,10 @@
 - Tolerance mode at its extremes (Eq. (15)): eps above every sigma keeps only the load
   column u_0 of each subdomain; eps far below keeps every sketched direction.
 - The smallest partition, two subdomains sharing one interface.
-- The widest sketch the kernels take, k = 79 (kp = 80 columns, the limit of the
-  shared-memory eigensolver and of the CG blocks), and the error beyond it.
+- The widest sketch of the small dense kernels, k = 79 (kp = 80 columns, the limit of
+  the shared-memory eigensolver); the narrowest sketch of the wide kernels, k = 80
+  (global-memory Jacobi, tiled Grams and row products); and the errors beyond the
+  limits (k <= 511 sketch columns, at most 128 basis columns per subdomain).
 - The mixed path at k = 1 (three of the four binary32 columns of a pack are padding)
   and at k = 79, within 1e-6 in energy of the binary64 path.
 
@@ -129,9 +131,25 @@ def test_widest_sketch_79_columns(mor, cube16):
     _mixed_close(mor, mesh, kappa, owner, p, rank, over, b, u)
 
 
-def test_sketch_wider_than_79_is_an_error(mor, cube16):
+def test_first_wide_sketch_80_columns(mor, cube16):
+    mesh, kappa, owner, p = cube16
+    rank, over = 70, 10
+    ref = pipeline.run(mesh, kappa, owner, rank, over, p["r_hops"], p["seed"],
+                       fe_solution=False)
+    b, info, u = _gpu(mor, mesh, kappa, owner, p["r_hops"], rank, over, p["seed"])
+    sg = b.sigma()
+    assert sg.shape[1] == 80
+    for i, ob in enumerate(ref["bases"]):
+        assert np.max(np.abs(sg[i] - ob["sigma"][:80])) <= 1e-10 * ob["sigma"][0]
+    assert np.array_equal(b.kept, [ob["n_kept"] for ob in ref["bases"]])
+    _same_solution(mesh, kappa, ref, info, u)
+
+
+def test_sketch_and_basis_width_limits_are_errors(mor, cube16):
     mesh, kappa, owner, p = cube16
     gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
     sd = mor.Subdomains(gm, owner, p["r_hops"])
-    with pytest.raises(mor.MorError, match="<= 79"):
-        mor.Bases(sd, mor.basis_opts(rank=70, oversample=10, seed=p["seed"]))
+    with pytest.raises(mor.MorError, match="<= 511"):
+        mor.Bases(sd, mor.basis_opts(rank=100, oversample=412, seed=p["seed"], eps=1e-30))
+    with pytest.raises(mor.MorError, match="<= 128"):
+        mor.Bases(sd, mor.basis_opts(rank=130, oversample=10, seed=p["seed"]))

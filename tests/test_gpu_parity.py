@@ -110,12 +110,46 @@ def test_bases_span_the_oracle_subspaces(cube16, oracle16, gpu16):
         assert sin_max <= 1e-10 / min(1.0, gap), (i, sin_max, gap)
 
 
+def _gap(sig, m):
+    return (sig[m - 1] - sig[m]) / sig[0]
+
+
 def test_projected_load_matches_oracle(cube16, oracle16, gpu16):
+    # b~_i = Q_i^T b_P depends on which A-orthonormal basis Q_i of the local space is
+    # chosen, but Q_i b~_i = Q_i Q_i^T b_P does not: two such bases differ by an
+    # orthogonal rotation O, and (Q O)(Q O)^T = Q Q^T.  Compare that vector element by
+    # element.
+    mesh, kappa, owner, p, sd = cube16
     bases = gpu16[0]
     bt = bases.bt()
     for i, b in enumerate(oracle16["bases"]):
-        # b~_i = Q_i^T b_P depends on the basis only through its span; compare norms
-        assert np.isclose(np.linalg.norm(bt[i]), np.linalg.norm(b["bt"]), rtol=1e-10)
+        Qg = bases.Q(i)[:, :bases.kept[i]]
+        got = Qg @ bt[i, :bases.kept[i]]
+        ref = b["Q"] @ b["bt"]
+        tol = 1e-10 / min(1.0, _gap(b["sigma"], p["rank"]))
+        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref)), i
+
+
+def test_interface_blocks_match_oracle_for_every_pair(cube16, oracle16, gpu16):
+    # K~_ij = Q_i^T A_0[P_i, P_j] Q_j (Eq. (23)) in the rotation-invariant form
+    # Q_i K~_ij Q_j^T = (Q_i Q_i^T) A_0[P_i, P_j] (Q_j Q_j^T), element by element over
+    # the owned nodes of both subdomains, for every neighbour pair of the batch
+    mesh, kappa, owner, p, sd = cube16
+    bases, red = gpu16[0], gpu16[1]
+    K = red.dense()
+    kq = bases.kq
+    off = reduced.offsets(oracle16["bases"])
+    Ko = oracle16["K"]
+    assert len(oracle16["pairs"]) > 0
+    for i, j in oracle16["pairs"]:
+        bi, bj = oracle16["bases"][i], oracle16["bases"][j]
+        ki, kj = bases.kept[i], bases.kept[j]
+        Kg = K[i * kq:i * kq + ki, j * kq:j * kq + kj]
+        got = bases.Q(i)[:, :ki] @ Kg @ bases.Q(j)[:, :kj].T
+        ref = bi["Q"] @ Ko[off[i]:off[i + 1], off[j]:off[j + 1]] @ bj["Q"].T
+        gap = min(_gap(bi["sigma"], p["rank"]), _gap(bj["sigma"], p["rank"]))
+        tol = 1e-10 / min(1.0, gap)
+        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref)), (i, j)
 
 
 def test_reduced_system_and_solution_match_oracle(cube16, oracle16, gpu16):
@@ -183,3 +217,28 @@ def test_full_rank_basis_reproduces_fe_solution(mor):
     u_fe = torch.as_tensor(ref["u"], device="cuda")
     err = mor.energy_norm(sd, u, u_fe) / mor.energy_norm(sd, u_fe)
     assert err < 1e-10, err
+
+
+def test_host_array_entry_point_gives_the_same_bases(mor, cube16, gpu16):
+    # mor_build_subdomains_host copies the mesh itself: the same plan (bit-exact index
+    # sets) and the same bases; the CG restriction sums use shared-memory atomics, whose
+    # order varies from run to run, so the results agree to rounding, not to the bit
+    mesh, kappa, owner, p, sd = cube16
+    sdh = mor.Subdomains.from_host(mesh.xyz, mesh.tets, kappa, mesh.dirichlet, owner,
+                                   p["r_hops"])
+    assert np.array_equal(sdh.counts, sd.counts)
+    for i in range(sd.n_sub):
+        for which in range(6):
+            assert np.array_equal(sdh.indices(i, which), sd.indices(i, which))
+    opts = mor.basis_opts(rank=p["rank"], oversample=p["oversample"], seed=p["seed"],
+                          precision="fp64", cg_rtol=1e-13)
+    bh = mor.Bases(sdh, opts)
+    b = gpu16[0]
+    s0 = b.sigma()
+    assert np.max(np.abs(bh.sigma() - s0)) <= 1e-12 * s0.max()
+    assert np.array_equal(bh.kept, b.kept)
+    for i in range(sd.n_sub):
+        Q1, Q0 = bh.Q(i)[:, :b.kept[i]], b.Q(i)[:, :b.kept[i]]
+        # the same span: the least-squares projection of one basis onto the other
+        P = Q0 @ np.linalg.lstsq(Q0, Q1, rcond=None)[0]
+        assert np.max(np.abs(P - Q1)) <= 1e-8 * np.max(np.abs(Q1))

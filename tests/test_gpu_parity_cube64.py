@@ -3,11 +3,16 @@ lognormal coefficient), in the launch configuration bench.py times (MOR_MIXED,
 cg_rtol 1e-9) and in binary64.
 
 The oracle computes sampled outputs one subdomain at a time: subdomain 0, the corner
-box, takes about 15 s on the CPU.  Every subdomain's index sets and the sketch
-right-hand side of sampled subdomains are checked too.  Properties that hold at any
-size are checked on the whole batch: K~ symmetric positive definite with identity
-diagonal blocks, Q_i^T A_ii Q_i = I, and the mixed-precision reduced solution within
-1e-6 relative energy of the binary64 one.
+box (|I| = 12,167), takes about 15 s on the CPU, and subdomain 21, an interior box
+with the largest extension (|I| = 27,080, the size that meets the 256-aggregate cap of
+the coarse level), about 40 s.  Sampled outputs: singular values, subspaces and the
+rotation-invariant projected load Q_i b~_i of subdomains 0 and 21, and the
+rotation-invariant interface blocks Q_i K~_ij Q_j^T of the neighbour pairs (0, 1) and
+(21, 22).  Every subdomain's index sets and the sketch right-hand side of sampled
+subdomains are checked too.  Properties that hold at any size are checked on the whole
+batch: K~ symmetric positive definite with identity diagonal blocks, Q_i^T A_ii Q_i = I,
+the reduced solution against a dense solve of the same K~, and the mixed-precision
+reduced solution within 1e-6 relative energy of the binary64 one.
 
 Tolerances: binary64 with cg_rtol 1e-11 perturbs the Gram G_B by ~1e-11 ||G_B||, so
 |ds| <= 1e-9 s_1 leaves two orders of margin; the subspace bound is that over the gap
@@ -19,6 +24,7 @@ import pytest
 
 import synth
 from oracle import basis as obasis
+from oracle import fem as ofem
 from oracle import subdomains as osub
 
 pytestmark = pytest.mark.gpu
@@ -42,11 +48,23 @@ def cube64(mor):
     return mesh, kappa, owner, p, sd
 
 
+SAMPLED = (0, 1, 21, 22)
+
+
 @pytest.fixture(scope="module")
-def oracle_sub0(cube64):
+def oracle64(cube64):
     mesh, kappa, owner, p, sd = cube64
-    s = osub.subdomain_sets(mesh, owner, 0, p["r_hops"])
-    return obasis.local_basis(mesh, kappa, s, p["rank"], p["oversample"], p["seed"])
+    adj = osub.node_adjacency(mesh.tets, mesh.n_nodes)
+    out = {}
+    for i in SAMPLED:
+        s = osub.subdomain_sets(mesh, owner, i, p["r_hops"], adj)
+        out[i] = obasis.local_basis(mesh, kappa, s, p["rank"], p["oversample"], p["seed"])
+    return out
+
+
+@pytest.fixture(scope="module")
+def oracle_sub0(oracle64):
+    return oracle64[0]
 
 
 @pytest.fixture(scope="module")
@@ -88,26 +106,83 @@ def test_sketch_rhs_sampled(mor, cube64):
         assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), i
 
 
-def test_sampled_singular_values_and_subspace(cube64, oracle_sub0, gpu64):
+def _gap(sig, m):
+    return (sig[m - 1] - sig[m]) / sig[0]
+
+
+@pytest.mark.parametrize("sub", [0, 21])
+def test_sampled_singular_values_and_subspace(cube64, oracle64, gpu64, sub):
     mesh, kappa, owner, p, sd = cube64
-    ref = oracle_sub0["sigma"]
+    ob = oracle64[sub]
+    if sub == 21:   # the interior box: the largest extension of the batch
+        assert sd.counts[sub, 0] == sd.counts[:, 0].max() == 27080
+    ref = ob["sigma"]
     m = p["rank"]
-    gap = (ref[m - 1] - ref[m]) / ref[0]
+    gap = _gap(ref, m)
     for prec, tol in (("fp64", 1e-9), ("mixed", 1e-7)):
         b = gpu64[prec][0]
-        sig = b.sigma()[0]
+        sig = b.sigma()[sub]
         n = min(len(ref), len(sig))
         assert np.max(np.abs(sig[:n] - ref[:n])) <= tol * ref[0], prec
-        A = oracle_sub0["A_PP"]
-        Qg = b.Q(0)[:, :b.kept[0]]
-        Qo = oracle_sub0["Q"]
+        A = ob["A_PP"]
+        Qg = b.Q(sub)[:, :b.kept[sub]]
+        Qo = ob["Q"]
         assert Qg.shape[1] == Qo.shape[1]
         R = Qg - Qo @ (Qo.T @ (A @ Qg))
         sin_max = np.sqrt(max(0.0, np.linalg.eigvalsh(R.T @ (A @ R)).max()))
         assert sin_max <= tol / min(1.0, gap), (prec, sin_max, gap)
-        bt = b.bt()[0]
-        assert np.isclose(np.linalg.norm(bt), np.linalg.norm(oracle_sub0["bt"]),
-                          rtol=10 * tol)
+        # Q_i b~_i = Q_i Q_i^T b_P does not depend on the rotation of Q_i
+        got = Qg @ b.bt()[sub, :b.kept[sub]]
+        want = Qo @ ob["bt"]
+        assert np.max(np.abs(got - want)) <= tol / min(1.0, gap) * np.max(np.abs(want)), prec
+
+
+@pytest.mark.parametrize("pair", [(0, 1), (21, 22)])
+def test_sampled_interface_blocks(cube64, oracle64, gpu64, pair):
+    # Eq. (23): K~_ij = Q_i^T A_0[P_i, P_j] Q_j, compared in the rotation-invariant form
+    # Q_i K~_ij Q_j^T on the interface rows and columns (the owned nodes of i and j
+    # coupled by A_0).  A_0[P_i, P_j] comes from the elements with vertices in both
+    # P_i and P_j, all of which lie in omega_0.
+    mesh, kappa, owner, p, sd = cube64
+    i, j = pair
+    oi, oj = oracle64[i], oracle64[j]
+    ow = owner[mesh.tets]
+    t = np.flatnonzero(np.any(ow == i, axis=1) & np.any(ow == j, axis=1))
+    G, vol = ofem.tet_geometry(mesh.xyz, mesh.tets[t])
+    fmap, free = ofem.free_map(mesh.dirichlet)
+    A0 = ofem.assemble_matrix(mesh.tets[t], ofem.stiffness_elements(G, vol, kappa[t]), fmap,
+                              len(free)).tocsr()
+    Aij = A0[fmap[oi["owned"]]][:, fmap[oj["owned"]]].toarray()
+    gi = np.flatnonzero(np.any(Aij != 0, axis=1))
+    gj = np.flatnonzero(np.any(Aij != 0, axis=0))
+    assert len(gi) > 0 and len(gj) > 0
+    ref = (oi["Q"][gi] @ (oi["Q"].T @ Aij @ oj["Q"])) @ oj["Q"][gj].T
+    gap = min(_gap(oi["sigma"], p["rank"]), _gap(oj["sigma"], p["rank"]))
+    for prec, tol in (("fp64", 1e-9), ("mixed", 1e-7)):
+        b, r = gpu64[prec][0], gpu64[prec][1]
+        K = r.dense()
+        kq = b.kq
+        ki, kj = b.kept[i], b.kept[j]
+        Kg = K[i * kq:i * kq + ki, j * kq:j * kq + kj]
+        got = b.Q(i)[gi, :ki] @ Kg @ b.Q(j)[gj, :kj].T
+        assert np.max(np.abs(got - ref)) <= tol / min(1.0, gap) * np.max(np.abs(ref)), prec
+
+
+def test_reduced_solve_matches_dense_solve_at_full_size(gpu64):
+    # the batched reduced CG (stopped at a relative residual of 1e-12) against LAPACK's
+    # Cholesky solve of the same K~ and b~: the error of x is at most cond(K~) times the
+    # residual, and the energy error is second order in it
+    import scipy.linalg as sla
+    for prec in ("fp64", "mixed"):
+        b, r, x, info, u = gpu64[prec]
+        K = r.dense()
+        bt = b.bt().ravel()
+        xd = sla.cho_solve(sla.cho_factor(K), bt)
+        xg = x.cpu().numpy()
+        ev = np.linalg.eigvalsh(K)
+        tol = 10.0 * (ev[-1] / ev[0]) * 1e-12
+        assert np.linalg.norm(xg - xd) <= tol * np.linalg.norm(xd), (prec, tol)
+        assert abs(info["energy"] - bt @ xd) <= 1e-10 * (bt @ xd), prec
 
 
 def test_reduced_matrix_properties_at_full_size(gpu64):

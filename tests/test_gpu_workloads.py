@@ -1,11 +1,13 @@
 """GPU path on the remaining workloads and on tolerance-mode truncation, against the
 oracle on sampled subdomains and against properties that hold at any size.
 
-- cube96_kmeans: an uneven batch. A 96^3 cube with interior nodes jittered by ±0.2h,
+- cube96_kmeans: an uneven batch (oracle on the two smallest and the largest
+  extended subdomains). A 96^3 cube with interior nodes jittered by ±0.2h,
   300 k-means subdomains (2k–4k owned nodes each), per-subdomain rank uniform in
   16..64 (sketch width rank + 10), and per-subdomain hops round(|P_i|^(1/3)/2).
-- cube128_p8_spheres: high contrast. A 128^3 cube with k = 1e4 in seeded spheres
-  (≥10% of the elements), 512 box subdomains, rank 48 + 10; local solves to 1e-11.
+- cube128_p8_spheres: high contrast (oracle on the corner box and an interior box).
+  A 128^3 cube with k = 1e4 in seeded spheres (≥10% of the elements), 512 box
+  subdomains, rank 48 + 10; local solves to 1e-11.
 - Tolerance mode (Eq. (15)) on the 16^3 cube: keep sigma_j > eps. eps is placed in the
   middle of a gap of the oracle's singular values, so the integer decision is not a
   rounding tie; the binary64 path must then keep the same number of directions.
@@ -115,9 +117,9 @@ def test_uneven_kmeans_batch(mor):
     for prec in out:
         assert np.all(out[prec][0].kept <= ranks + 1)
         assert np.all(out[prec][0].kept >= ranks)
-    # sampled oracle checks: the smallest extended subdomains
+    # sampled oracle checks: the two smallest extended subdomains and the largest
     sizes = sd.counts[:, 0] + sd.counts[:, 1]
-    subs = list(np.argsort(sizes)[:2])
+    subs = list(np.argsort(sizes)[:2]) + [int(np.argmax(sizes))]
     _check_sampled(mesh, kappa, owner, p, sd, out, subs, lambda i: int(ranks[i]))
     _check_batch(mor, sd, out)
 
@@ -133,7 +135,10 @@ def test_high_contrast_spheres(mor):
     # path needs cg_rtol 1e-11 (not 1e-9) for 1e-6 relative energy.  Columns that reach
     # the rounding level of the binary64 residual first stop there.
     out = _build_both(mor, sd, p, mixed_rtol=1e-11)
-    _check_sampled(mesh, kappa, owner, p, sd, out, [0], lambda i: p["rank"])
+    # the corner box and an interior box (3, 3, 3), whose extension is the largest
+    interior = 3 + 8 * (3 + 8 * 3)
+    assert sd.counts[interior, 0] == sd.counts[:, 0].max()
+    _check_sampled(mesh, kappa, owner, p, sd, out, [0, interior], lambda i: p["rank"])
     _check_batch(mor, sd, out)
 
 

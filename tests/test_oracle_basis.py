@@ -213,3 +213,21 @@ def test_weighted_h1_form_reduces_to_the_paper_form_for_unit_coefficient():
     d = basis.local_basis(mesh, kappa, s, p["rank"], p["oversample"], p["seed"],
                           h1_weighted=True)
     assert not np.allclose(c["sigma"], d["sigma"])   # the variant is not a no-op
+
+
+def test_gram_form_of_the_weighted_svd_equals_the_printed_form(cube16):
+    # Eq. (24) as printed (SVD of B = Qh^T R_i Z R_BB^{-1} with R_BB from the Cholesky
+    # factor of H^+) and the Gram form B B^T = T^T S_B^{-1} T (Lemma 4.1: S_B = R_BB^T
+    # R_BB, and S_B^{-1} is the B block of (H^+)^{-1}) give the same singular values
+    # and the same basis; large subdomains use the Gram form in the oracle
+    mesh, kappa, owner, p, subs = cube16
+    for i in (0, 6):
+        a = basis.local_basis(mesh, kappa, subs[i], 8, 5, 11, rbb="always")
+        b = basis.local_basis(mesh, kappa, subs[i], 8, 5, 11, rbb="never")
+        assert b["R_BB"] is None and a["R_BB"] is not None
+        assert np.max(np.abs(a["sigma"] - b["sigma"])) <= 1e-12 * a["sigma"][0]
+        A = a["A_PP"]
+        R = b["Q"] - a["Q"] @ (a["Q"].T @ (A @ b["Q"]))
+        sin_max = np.sqrt(max(0.0, np.linalg.eigvalsh(R.T @ (A @ R)).max()))
+        gap = (a["sigma"][7] - a["sigma"][8]) / a["sigma"][0]
+        assert sin_max <= 1e-11 / min(1.0, gap)

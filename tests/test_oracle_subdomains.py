@@ -72,3 +72,30 @@ def test_overlap_is_one_element_layer():
         cover[s["omega_tets"]] += 1
     assert np.array_equal(np.flatnonzero(cover >= 2), t0)
     assert cover.min() == 1
+
+
+def test_region_sets_equal_whole_mesh_sets():
+    # the restricted computation (for meshes too large for a global adjacency) gives
+    # the sets of the whole-mesh computation when its candidate elements reach r + 2
+    # cells beyond the owned box; with too small a region it must not silently agree
+    n, parts, r = 24, 3, 4
+    mesh = synth.kuhn_cube(n)
+    owner = synth.box_owner(n, parts)
+    adj = sd.node_adjacency(mesh.tets, mesh.n_nodes)
+    for i in (0, 4, 13, 26):
+        a = (i % parts, (i // parts) % parts, i // parts ** 2)
+        rng = [synth.box_node_range(n, parts, v) for v in a]
+        lo = [x[0] - r - 2 for x in rng]
+        hi = [x[1] + r + 1 for x in rng]
+        reg = synth.kuhn_box_tets(n, lo, hi)
+        got = sd.subdomain_sets_region(mesh, owner, i, r, reg)
+        ref = sd.subdomain_sets(mesh, owner, i, r, adj)
+        for key in ("I", "B", "omega", "owned", "plus_tets", "omega_tets"):
+            assert np.array_equal(got[key], ref[key]), (i, key)
+    # a region one hop short misclassifies boundary nodes of the extension
+    i = 13
+    rng = [synth.box_node_range(n, parts, 1) for _ in range(3)]
+    reg = synth.kuhn_box_tets(n, [x[0] - r + 1 for x in rng], [x[1] + r - 1 for x in rng])
+    got = sd.subdomain_sets_region(mesh, owner, i, r, reg)
+    ref = sd.subdomain_sets(mesh, owner, i, r, adj)
+    assert not np.array_equal(got["B"], ref["B"])

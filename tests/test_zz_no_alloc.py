@@ -7,7 +7,9 @@ fixed device work array inside the library.  This test builds the reduced system
 16^3 workload through the handle API, hands the same block-sparse matrix and load to the
 allocation-free entry point through the C ABI (inputs and output allocated here by the
 test), and checks two calls in a row against the handle solve within the 1e-10 relative
-tolerance used for the reduced solution elsewhere.
+tolerance used for the reduced solution elsewhere.  The second call must leave the
+device's free memory and PyTorch's allocated memory unchanged: after the first call on
+a device has set up the fixed array, the entry point allocates nothing.
 """
 import ctypes
 
@@ -65,13 +67,24 @@ def test_noalloc_reduced_solve_matches_handle_solve():
     bt_d = torch.as_tensor(bases.bt().ravel(), device=dev)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     P = lambda t: ctypes.c_void_p(t.data_ptr())
+    # both outputs are allocated before the first call, so that nothing else allocates
+    # between the two calls
+    xs = [torch.full((n_sub * kq,), float("nan"), dtype=torch.float64, device=dev)
+          for _ in range(2)]
+    torch.cuda.synchronize()
+    mem = None
     for call in range(2):
-        x_d = torch.full((n_sub * kq,), float("nan"), dtype=torch.float64, device=dev)
+        x_d = xs[call]
         info = mor.SolveInfo()
         rc = mor._lib.mor_solve_reduced_noalloc(n_sub, kq, P(ptr_d), P(sub_d), P(blk_d),
                                                 P(blocks_d), P(bt_d), 1e-13, 20000, stream,
                                                 P(x_d), ctypes.byref(info))
         assert rc == 0, mor._lib.mor_last_error()
+        torch.cuda.synchronize()
+        now = (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated())
+        if mem is not None:
+            assert now == mem, "the second call changed device memory use: %s -> %s" % (mem, now)
+        mem = now
         x = x_d.cpu().numpy()
         assert info.converged == 1
         assert np.max(np.abs(x - x_ref)) <= 1e-10 * np.max(np.abs(x_ref)), call
@@ -87,7 +100,10 @@ def test_noalloc_rejects_systems_beyond_its_fixed_scratch():
     one = torch.zeros(8, dtype=torch.float64, device="cuda")
     idx = torch.zeros(8, dtype=torch.int32, device="cuda")
     P = lambda t: ctypes.c_void_p(t.data_ptr())
-    rc = mor._lib.mor_solve_reduced_noalloc(70000, 8, P(idx), P(idx), P(idx), P(one), P(one),
-                                            1e-10, 10, None, P(one), None)
-    assert rc == -1
-    assert b"too large" in mor._lib.mor_last_error()
+    # each limit on its own: too many subdomains (dim within its limit), and too many
+    # unknowns (subdomains within theirs)
+    for n_sub, kq in ((65537, 1), (1000, 600)):
+        rc = mor._lib.mor_solve_reduced_noalloc(n_sub, kq, P(idx), P(idx), P(idx), P(one),
+                                                P(one), 1e-10, 10, None, P(one), None)
+        assert rc == -1, (n_sub, kq)
+        assert b"too large" in mor._lib.mor_last_error()
