@@ -419,6 +419,7 @@ def ours(args):
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": int(launches),
+        "autotune": mor.autotune_report(),
         "clocks": clk,
         "a1_host_ms": a1_ms,
         "local_solve_iterations": b.stats()[:5].tolist(),

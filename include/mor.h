@@ -186,6 +186,11 @@ typedef struct {
                           check; sub_end <= 0 means all.  The draws of a subdomain do
                           not depend on the range.  One-shot plans require the whole
                           range (MOR_ERR_ARG otherwise).                                */
+  int32_t tc_gram;     /* MOR_MIXED: 1 (default) runs the dense contractions (the
+                          H_i-Grams, G_B, V^T A V and the interface blocks of step 3) on
+                          the tensor cores (tcgen05, exact 7-bit bf16 slices, about 2^-28
+                          relative per column pair); 0 keeps them in binary64 SIMT.
+                          MOR_FP64 always uses binary64.                                */
   int32_t explicit_svd; /* 1: the explicit weighted SVD of Eq. (14) instead of the
                           randomized one: dense Cholesky factors of A_II, H_i and H^+
                           (R_i, R_BB, Lemma 4.1), Z_i = C_i A_II^{-1} A_IB, and the
@@ -197,7 +202,7 @@ typedef struct {
 /* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
  * max_iter 20000, replace_every 40, normwise 1, drift_restart 1.5, sketch_rtol 0,
  * tau 1e-12, orth_tol 1e-14, coarse_rows 100, h1_weighted 0, sketch_div 0, sub_begin 0,
- * sub_end 0, explicit_svd 0). */
+ * sub_end 0, tc_gram 1, explicit_svd 0). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 
 /* Step 2 for every subdomain in one batch (Sec. 4, Sec. 6 step 2, Eq. (24)):
@@ -352,6 +357,15 @@ int mor_debug_plan_check(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
 int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts,
                          int32_t sub, double* out, void* stream);
 
+/* Debug/parity access: G = X^T Y on the tensor cores, as the mixed path computes its
+ * Grams (tcgen05 MMAs on exact 7-bit bf16 slices, FP32 accumulators in TMEM, binary64
+ * combination; see mor_basis_opts.tc_gram).  X_dev [device, rows x nx], Y_dev [device,
+ * rows x ny] row-major binary64, nx, ny <= 128; G_dev [device, nx x ny] is written.
+ * Allocates its work space.  The paper has no counterpart (its contractions are
+ * binary64). */
+int mor_debug_tc_gram(int64_t rows, int32_t nx, int32_t ny, const double* X_dev,
+                      const double* Y_dev, double* G_dev, void* stream);
+
 /* Kernel timing for the roofline: when enabled, the four kernels of every local CG
  * step of mor_build_bases are bracketed by CUDA events on the launching stream.
  * mor_profile_query fills out[host, 4] = {launches, total milliseconds, algorithmic
@@ -369,6 +383,19 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts,
 int mor_profile_enable(int32_t on);
 int mor_profile_reset(void);
 int mor_profile_query(int32_t family, double* out);
+
+/* Autotuner of the local solves' sparse product q = A p (with the p.q sums): the first
+ * product of each (precision, column count, slot width) the process meets is timed in
+ * four launch configurations (1 or 2 slot records gathered per batch, blocks of 256 or
+ * 128 threads; CUDA events, three launches each after one warm-up) and the fastest is
+ * used from then on.  All four give the same bits.  mor_autotune(0) turns tuning off
+ * (the first configuration is used where nothing is cached), mor_autotune(-1) clears the
+ * cache.  mor_autotune_report fills out[host, 8 x max_entries] with {binary64, columns,
+ * slot width, chosen configuration, microseconds of configurations 0..3} per entry and
+ * *n with the entry count.  Process-wide, not thread-safe.  The paper has no
+ * counterpart. */
+int mor_autotune(int32_t on);
+int mor_autotune_report(int64_t* out, int32_t max_entries, int32_t* n);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (host-side counter), into *out. */

@@ -22,7 +22,7 @@ LIB = os.path.join(LIBDIR, "libmor.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["mor_api.cu", "mor_assembly.cu", "mor_sparse.cu", "mor_dense.cu",
               "mor_reduced.cu", "mor_noalloc.cu", "mor_coarse.cu", "mor_wide.cu",
-              "mor_explicit.cu"]
+              "mor_explicit.cu", "mor_tc.cu"]
 CPP_SOURCES = ["mor_plan.cpp"]
 
 

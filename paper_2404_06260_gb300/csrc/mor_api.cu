@@ -232,6 +232,7 @@ struct mor_bases_s {
   double* Rbb = nullptr;
   std::vector<int64_t> rbb_off;
   std::vector<int32_t> rbb_m;
+  bool tc = false;  // mixed precision with tensor-core contractions (step 3 follows)
   double *Q = nullptr, *bt = nullptr, *sigma = nullptr;
   int* kept = nullptr;
   std::vector<int32_t> h_kept;
@@ -506,6 +507,7 @@ int mor_basis_opts_default(mor_basis_opts* o) {
   o->coarse_rows = 100;
   o->h1_weighted = 0;
   o->sketch_div = 0;
+  o->tc_gram = 1;
   o->explicit_svd = 0;
   o->sub_begin = 0;
   o->sub_end = 0;
@@ -1074,9 +1076,24 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   TRY(M.alloc(&gcnt, n_sd, true, st));
   TRY(M.alloc(&kcnt, n_sd, true, st));
   // the small kernels serve widths up to 80 columns, the wide ones the rest
+  // tensor-core Grams (mixed precision): partials per (subdomain, row chunk)
+  const bool use_tc = B.mixed && o.tc_gram != 0;
+  double* tcpart = nullptr;
+  int64_t* tcrange = nullptr;
+  int* tcerr = nullptr;
+  if (use_tc) {
+    const size_t n = (size_t)std::min(std::max(kb, 4), 128);
+    TRY(M.alloc(&tcpart, (size_t)n_sd * tc_gram_chunks(n_sd) * n * n, false, st));
+    TRY(M.alloc(&tcrange, (size_t)2 * n_sd, true, st));
+    TRY(M.alloc(&tcerr, 1, true, st));
+  }
+  const long long tc_budget = wait_budget_cycles();
   auto gram = [&](const DTiles& tl, const double* X, int ldx, int nx, const double* Y,
                   int ldy, int ny, int ldg) {
-    if (nx > 80 || ny > 80)
+    if (use_tc && nx <= 128 && ny <= 128)
+      launch_tc_gram(tl, n_sd, X, ldx, nx, Y, ldy, ny, tcpart, tcrange, G, ldg,
+                     (int64_t)ldg * ldg, tc_budget, tcerr, st);
+    else if (nx > 80 || ny > 80)
       launch_gram_wide(tl, n_sd, X, ldx, nx, Y, ldy, ny, gpart, G, ldg, (int64_t)ldg * ldg,
                        st);
     else
@@ -1359,6 +1376,15 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
     Bo.rbb_off = DW.h_bboff;
     Bo.rbb_m = DW.h_M;
   }
+  if (use_tc) {
+    int h_tcerr = 0;
+    CK(cudaMemcpyAsync(&h_tcerr, tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_tcerr)
+      return fail(MOR_ERR_TIMEOUT, "mor_build_bases: a tensor-core Gram's wait ran out of its "
+                                   "budget (mor_set_wait_budget)");
+    Bo.tc = true;
+  }
   Bo.h_kept.resize(n_sd);
   Bo.h_sigma.resize((size_t)n_sd * Bo.kp);
   CK(cudaMemcpyAsync(Bo.h_kept.data(), Bo.kept, n_sd * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1455,6 +1481,7 @@ static int build_bases_streamed(const mor_subdomains* sd, const mor_basis_opts* 
     if (first) {
       first = false;
       Bo.n_sd = g.n_sd;
+      Bo.tc = wb->tc;
       Bo.k = wb->k;
       Bo.kp = wb->kp;
       Bo.kq = wb->kq;
@@ -1567,8 +1594,27 @@ int mor_project(const mor_subdomains* sd, const mor_bases* b, void* stream, mor_
   launch_iface_vals(sd->n_iface, sd->e_unode, sd->e_vnode, sd->n2t_ptr, sd->n2t, sd->xyz,
                     sd->tets, sd->kappa, aval, st);
   TRY(A.alloc(&r->blocks, (size_t)2 * std::max(r->n_pairs, 1) * b->kq * b->kq, true, st));
-  launch_pair_blocks(r->n_pairs, sd->pair_ptr, sd->e_urow, sd->e_vrow, aval, b->Q, b->kq,
-                     r->blocks, st);
+  if (b->tc && b->kq <= 128) {
+    // K~_ij = sum over interface entries of a_e Q[u_e]^T Q[v_e] on the tensor cores
+    Allocs W;
+    W.use_pool(st);
+    double *part, *Gp;
+    int* err;
+    const size_t nb = (size_t)std::max(r->n_pairs, 1) * b->kq * b->kq;
+    TRY(W.alloc(&part, nb, false, st));
+    TRY(W.alloc(&Gp, nb, false, st));
+    TRY(W.alloc(&err, 1, true, st));
+    launch_tc_pair_blocks(r->n_pairs, sd->pair_ptr, sd->e_urow, sd->e_vrow, aval, b->Q, b->kq,
+                          part, Gp, r->blocks, wait_budget_cycles(), err, st);
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h)
+      return fail(MOR_ERR_TIMEOUT, "mor_project: a tensor-core wait ran out of its budget");
+  } else {
+    launch_pair_blocks(r->n_pairs, sd->pair_ptr, sd->e_urow, sd->e_vrow, aval, b->Q, b->kq,
+                       r->blocks, st);
+  }
   TRY(A.alloc(&r->bt, r->dim, false, st));
   CK(cudaMemcpyAsync(r->bt, b->bt, r->dim * sizeof(double), cudaMemcpyDeviceToDevice, st));
   r->h_nbr_ptr = sd->nbr_ptr;
@@ -1842,6 +1888,30 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts, i
   return MOR_OK;
 }
 
+int mor_debug_tc_gram(int64_t rows, int32_t nx, int32_t ny, const double* X_dev,
+                      const double* Y_dev, double* G_dev, void* stream) {
+  if (rows < 0 || nx < 1 || ny < 1 || nx > 128 || ny > 128 || !G_dev ||
+      (rows > 0 && (!X_dev || !Y_dev)))
+    return fail(MOR_ERR_ARG, "mor_debug_tc_gram: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Allocs A;
+  A.use_pool(st);
+  double* part;
+  int64_t* range;
+  int* err;
+  TRY(A.alloc(&part, (size_t)nx * ny, false, st));
+  TRY(A.alloc(&range, 2, true, st));
+  TRY(A.alloc(&err, 1, true, st));
+  launch_tc_gram_rows(rows, X_dev, nx, nx, Y_dev, ny, ny, part, range, G_dev,
+                      wait_budget_cycles(), err, st);
+  int h = 0;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h) return fail(MOR_ERR_TIMEOUT, "mor_debug_tc_gram: a wait ran out of its budget");
+  return MOR_OK;
+}
+
 int mor_profile_enable(int32_t on) {
   g_prof.on = on != 0;
   return MOR_OK;
@@ -1859,6 +1929,21 @@ int mor_profile_query(int32_t family, double* out) {
   out[3] = 0;
   return MOR_OK;
 }
+int mor_autotune(int32_t on) {
+  if (on < 0)
+    autotune_reset();
+  else
+    autotune_enable(on != 0);
+  return MOR_OK;
+}
+
+int mor_autotune_report(int64_t* out, int32_t max_entries, int32_t* n) {
+  if (!n || max_entries < 0 || (max_entries > 0 && !out))
+    return fail(MOR_ERR_ARG, "mor_autotune_report: bad argument");
+  *n = autotune_entries(out, max_entries);
+  return MOR_OK;
+}
+
 int mor_kernel_launches(int64_t* out) {
   if (!out) return fail(MOR_ERR_ARG, "mor_kernel_launches: null");
   *out = (int64_t)g_kernel_launches.load();

@@ -266,6 +266,24 @@ void launch_trmv_upper(int n_sd, int n_max, int ncol_max, const double* U, const
 void launch_node_normals(int n_sd, int m_max, const int32_t* bnode, const int64_t* boff,
                          const int32_t* mm, const int32_t* kk, int k, uint64_t seed,
                          uint32_t sd_base, double* out, int ld, cudaStream_t st);
+// tensor-core Grams (mor_tc.cu), columns nx, ny <= 128: partial buffers of
+// n_items * tc_gram_chunks(n_items) * nx * ny doubles, range of 2 * n_items int64, err
+// set when a bounded wait ran out
+int tc_gram_chunks(int n_items);
+void launch_tc_gram(const DTiles& tiles, int n_sd, const double* X, int ldx, int nx,
+                    const double* Y, int ldy, int ny, double* part, int64_t* range, double* G,
+                    int ldg, int64_t stride, long long budget, int* err, cudaStream_t st);
+void launch_tc_pair_blocks(int n_pairs, const int64_t* pair_ptr, const int32_t* urow,
+                           const int32_t* vrow, const double* aval, const double* Q, int kq,
+                           double* part, double* G, double* blocks, long long budget, int* err,
+                           cudaStream_t st);
+void launch_tc_gram_rows(int64_t rows, const double* X, int ldx, int nx, const double* Y,
+                         int ldy, int ny, double* part, int64_t* range, double* G,
+                         long long budget, int* err, cudaStream_t st);
+// autotuner of the sparse product (mor_sparse.cu)
+void autotune_enable(bool on);
+void autotune_reset();
+int autotune_entries(int64_t* out, int max_entries);
 void launch_gather_rows(int64_t n_rows, const int32_t* map, const double* src, int lds,
                         int sc0, double* dst, int ldd, int dc0, int ncols, cudaStream_t st);
 // dst[map[r], c] = src[r, c]

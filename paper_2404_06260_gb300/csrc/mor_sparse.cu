@@ -8,6 +8,9 @@
 // last tile of a subdomain to finish (atomic ticket) reduces them in tile order, so the
 // reductions are deterministic and need no extra launch.
 #include "mor_kernels.h"
+
+#include <mutex>
+#include <vector>
 #include "mor_plan.h"
 
 namespace mor {
@@ -220,8 +223,10 @@ __device__ __forceinline__ void stage_tile(const Geo& g, int r0, int nrows,
   }
 }
 
-// row rr of the staged tile (slice width w) times X: column chunk tx
-template <typename T>
+// row rr of the staged tile (slice width w) times X: column chunk tx.  R records (2 R
+// slots) are gathered per batch before their multiply-adds, which run in slot order
+// (the sum is the same for every R).
+template <typename T, int R = 1>
 __device__ __forceinline__ Pack<T> spmm_row(int rr, int w, int tx, const Slot2<T>* slots,
                                             const T* __restrict__ X, int kp) {
   constexpr int N = Pack<T>::N;
@@ -229,22 +234,33 @@ __device__ __forceinline__ Pack<T> spmm_row(int rr, int w, int tx, const Slot2<T
 #pragma unroll
   for (int e = 0; e < N; ++e) acc.v[e] = T(0);
   const int w2 = (w + 1) >> 1;
-  for (int h = 0; h < w2; ++h) {
-    const Slot2<T> rec = slots[h * kTileRows + rr];
-    Pack<T> xv[2];
+  for (int h0 = 0; h0 < w2; h0 += R) {
+    Slot2<T> rec[R];
+    Pack<T> xv[2 * R];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      if (rec.c[u] >= 0) {
-        xv[u] = ld(X + (int64_t)rec.c[u] * kp + tx * N);
+    for (int g = 0; g < R; ++g) {
+      if (h0 + g < w2) {
+        rec[g] = slots[(h0 + g) * kTileRows + rr];
       } else {
+        rec[g].c[0] = rec[g].c[1] = -1;
+        rec[g].v[0] = rec[g].v[1] = T(0);
+      }
 #pragma unroll
-        for (int e = 0; e < N; ++e) xv[u].v[e] = T(0);
+      for (int u = 0; u < 2; ++u) {
+        if (rec[g].c[u] >= 0) {
+          xv[2 * g + u] = ld(X + (int64_t)rec[g].c[u] * kp + tx * N);
+        } else {
+#pragma unroll
+          for (int e = 0; e < N; ++e) xv[2 * g + u].v[e] = T(0);
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int g = 0; g < R; ++g)
 #pragma unroll
-      for (int e = 0; e < N; ++e) acc.v[e] += rec.v[u] * xv[u].v[e];
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int e = 0; e < N; ++e) acc.v[e] += rec[g].v[u] * xv[2 * g + u].v[e];
   }
   return acc;
 }
@@ -310,9 +326,10 @@ __device__ __forceinline__ void spmm_row_res(int rr, int w, int tx, const Slot2<
   }
 }
 
-// at most 256 threads (kp <= 80 columns): 40 registers leave room for six blocks per SM
-template <typename T>
-__global__ void __launch_bounds__(256, 6)
+// at most TH threads per block; 40 registers leave room for 1536 threads per SM (six
+// blocks of 256, twelve of 128).  R: records gathered per batch (spmm_row)
+template <typename T, int R = 1, int TH = 256>
+__global__ void __launch_bounds__(TH, 1536 / TH)
     k_cg_spmm_pq(DTiles tl, EllView<T> A, const T* __restrict__ p, T* __restrict__ q, int kp,
                  CgState s) {
   constexpr int N = Pack<T>::N;
@@ -329,7 +346,7 @@ __global__ void __launch_bounds__(256, 6)
   const int rend = pack_done<T>(s, sd, kp, g.tx) ? 0 : r1 - r0;
   for (int rr = g.ty; rr < rend; rr += g.rb) {
     int64_t row = r0 + rr;
-    Pack<T> qv = spmm_row(rr, A.width[row >> 5], g.tx, sm.slots, p, kp);
+    Pack<T> qv = spmm_row<T, R>(rr, A.width[row >> 5], g.tx, sm.slots, p, kp);
     int64_t o = row * kp + g.tx * N;
     st(q + o, qv);
     Pack<T> pv = ld(p + o);
@@ -979,9 +996,9 @@ __global__ void k_cast(DTiles tl, const double* __restrict__ src, T* __restrict_
 }
 
 template <typename T>
-dim3 block_of(int kp) {
+dim3 block_of(int kp, int threads = 256) {
   int nch = kp / Pack<T>::N;
-  int rb = 256 / nch;
+  int rb = threads / nch;
   if (rb < 1) rb = 1;
   return dim3(nch, rb);
 }
@@ -1051,6 +1068,74 @@ void launch_cg_init(const DTiles& tiles, const T* b, T* x, T* r, T* p, const T* 
                           nullptr);
 }
 
+// ---- autotuner of the sparse product: four launch configurations of k_cg_spmm_pq
+// (1 or 2 records per gather batch, blocks of 256 or 128 threads), timed on the first
+// product of each (precision, column count, slot width) the process meets, the fastest
+// kept for the rest of the process.  The product is a pure function of p (q, its
+// column sums and the step length are rewritten), so timing it on live data changes
+// no result.
+constexpr int kSpmmVariants = 4;
+template <typename T>
+void launch_spmm_pq_variant(int v, const DTiles& tiles, const EllView<T>& A, const T* p, T* q,
+                            int kp, const CgState& s, cudaStream_t st) {
+  const int th = (v & 2) ? 128 : 256;
+  dim3 bl = block_of<T>(kp, th);
+  const size_t sm = smem_bytes<T>(bl.x, bl.y, kp, A.W);
+  switch (v) {
+    case 0: k_cg_spmm_pq<T, 1, 256><<<tiles.n, bl, sm, st>>>(tiles, A, p, q, kp, s); break;
+    case 1: k_cg_spmm_pq<T, 2, 256><<<tiles.n, bl, sm, st>>>(tiles, A, p, q, kp, s); break;
+    case 2: k_cg_spmm_pq<T, 1, 128><<<tiles.n, bl, sm, st>>>(tiles, A, p, q, kp, s); break;
+    default: k_cg_spmm_pq<T, 2, 128><<<tiles.n, bl, sm, st>>>(tiles, A, p, q, kp, s); break;
+  }
+}
+
+struct TuneEntry {
+  int wide, kp, W, variant;
+  float ms[kSpmmVariants];
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+bool g_tune_on = true;
+
+template <typename T>
+int spmm_variant(const DTiles& tiles, const EllView<T>& A, const T* p, T* q, int kp,
+                 const CgState& s, cudaStream_t st) {
+  const int wide = sizeof(T) == 8 ? 1 : 0;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto& e : g_tune)
+    if (e.wide == wide && e.kp == kp && e.W == A.W) return e.variant;
+  if (!g_tune_on || kp / Pack<T>::N > 128) return 0;
+  static bool attr = false;
+  if (!attr) {
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T, 1, 256>);
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T, 2, 256>);
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T, 1, 128>);
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T, 2, 128>);
+    attr = true;
+  }
+  TuneEntry e{wide, kp, A.W, 0, {0, 0, 0, 0}};
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (int v = 0; v < kSpmmVariants; ++v) {
+    launch_spmm_pq_variant<T>(v, tiles, A, p, q, kp, s, st);  // warm-up
+    cudaEventRecord(a, st);
+    for (int rep = 0; rep < 3; ++rep) launch_spmm_pq_variant<T>(v, tiles, A, p, q, kp, s, st);
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    e.ms[v] = t / 3.0f;
+    count_launch(4);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  for (int v = 1; v < kSpmmVariants; ++v)
+    if (e.ms[v] < e.ms[e.variant]) e.variant = v;
+  g_tune.push_back(e);
+  return e.variant;
+}
+
 template <typename T>
 void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, T* q,
                     const T* dinv, int kp, double tol2, const CgState& s, const Coarse<T>& co,
@@ -1058,15 +1143,18 @@ void launch_cg_step(const DTiles& tiles, const EllView<T>& A, T* x, T* r, T* p, 
   if (tiles.n <= 0) return;
   static bool attr = false;
   if (!attr) {
-    set_smem_attr<T>((const void*)k_cg_spmm_pq<T>);
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T, 1, 256>);
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T, 2, 256>);
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T, 1, 128>);
+    set_smem_attr<T>((const void*)k_cg_spmm_pq<T, 2, 128>);
     set_smem_attr<T>((const void*)k_cg_update_xr<T>);
     attr = true;
   }
   dim3 bl = block_of<T>(kp);
+  const int variant = spmm_variant<T>(tiles, A, p, q, kp, s, st);
   count_launch(2);
   if (ev) cudaEventRecord(ev[0], st);
-  k_cg_spmm_pq<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, A.W), st>>>(tiles, A, p, q, kp,
-                                                                           s);
+  launch_spmm_pq_variant<T>(variant, tiles, A, p, q, kp, s, st);
   if (ev) cudaEventRecord(ev[1], st);
   k_cg_update_xr<T><<<tiles.n, bl, slot_kernel_smem<T>(bl, kp), st>>>(tiles, x, r, p, q, dinv,
                                                                        kp, s, co);
@@ -1198,4 +1286,29 @@ template void launch_cg_step<double>(const DTiles&, const EllView<double>&, doub
                                      double*, double*, const double*, int, double,
                                      const CgState&, const Coarse<double>&, cudaStream_t,
                                      const cudaEvent_t*);
+void autotune_enable(bool on) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_on = on;
+}
+
+void autotune_reset() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.clear();
+}
+
+int autotune_entries(int64_t* out, int max_entries) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  const int n = (int)g_tune.size();
+  for (int i = 0; i < n && i < max_entries; ++i) {
+    const TuneEntry& e = g_tune[i];
+    int64_t* o = out + 8 * (int64_t)i;
+    o[0] = e.wide;
+    o[1] = e.kp;
+    o[2] = e.W;
+    o[3] = e.variant;
+    for (int v = 0; v < kSpmmVariants; ++v) o[4 + v] = (int64_t)(1e3 * e.ms[v]);  // us
+  }
+  return n;
+}
+
 }  // namespace mor

@@ -48,7 +48,7 @@ class BasisOpts(ctypes.Structure):
                 ("sketch_rtol", _dbl), ("tau", _dbl), ("orth_tol", _dbl),
                 ("coarse_rows", _i32), ("h1_weighted", _i32), ("sketch_div", _i32),
                 ("sub_begin", _i32),
-                ("sub_end", _i32), ("explicit_svd", _i32)]
+                ("sub_end", _i32), ("tc_gram", _i32), ("explicit_svd", _i32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -90,11 +90,14 @@ _sig("mor_lift", _i32, _P, _P, _P, _P, _P)
 _sig("mor_set_wait_budget", _i32, _dbl)
 _sig("mor_debug_wait_timeout", _i32, _dbl, ctypes.POINTER(_i32))
 _sig("mor_energy_norm", _i32, _P, _P, _P, ctypes.POINTER(_dbl), _P)
+_sig("mor_debug_tc_gram", _i32, _i64, _i32, _i32, _P, _P, _P, _P)
 _sig("mor_debug_sketch_rhs", _i32, _P, ctypes.POINTER(BasisOpts), _i32, _P, _P)
 _sig("mor_profile_enable", _i32, _i32)
 _sig("mor_profile_reset", _i32)
 _sig("mor_profile_query", _i32, _i32, _P)
 _sig("mor_kernel_launches", _i32, ctypes.POINTER(_i64))
+_sig("mor_autotune", _i32, _i32)
+_sig("mor_autotune_report", _i32, _P, _i32, ctypes.POINTER(_i32))
 _sig("mor_free_subdomains", None, _P)
 _sig("mor_free_bases", None, _P)
 _sig("mor_free_reduced", None, _P)
@@ -109,8 +112,10 @@ EXPORTED = ["mor_build_subdomains", "mor_build_subdomains_host",
             "mor_solve_reduced_noalloc", "mor_set_wait_budget", "mor_debug_wait_timeout",
             "mor_lift",
             "mor_energy_norm", "mor_debug_sketch_rhs", "mor_debug_plan_check",
+            "mor_debug_tc_gram",
             "mor_profile_enable",
-            "mor_profile_reset", "mor_profile_query", "mor_kernel_launches", "mor_free_subdomains",
+            "mor_profile_reset", "mor_profile_query", "mor_kernel_launches", "mor_autotune",
+            "mor_autotune_report", "mor_free_subdomains",
             "mor_free_bases", "mor_free_reduced", "mor_last_error"]
 
 
@@ -380,6 +385,17 @@ def sketch_rhs(sd: Subdomains, opts: BasisOpts, sub: int, stream=None) -> np.nda
     return out
 
 
+def tc_gram(X, Y, stream=None):
+    """G = X^T Y on the tensor cores (mor_debug_tc_gram); X, Y binary64 CUDA tensors."""
+    assert X.is_cuda and Y.is_cuda and X.dtype == torch.float64 and Y.dtype == torch.float64
+    X, Y = X.contiguous(), Y.contiguous()
+    G = torch.empty((X.shape[1], Y.shape[1]), dtype=torch.float64, device=X.device)
+    _check(_lib.mor_debug_tc_gram(int(X.shape[0]), int(X.shape[1]), int(Y.shape[1]),
+                                  _P(X.data_ptr()), _P(Y.data_ptr()), _P(G.data_ptr()),
+                                  _stream(stream)))
+    return G
+
+
 def profile(on: bool):
     _check(_lib.mor_profile_enable(1 if on else 0))
 
@@ -397,6 +413,22 @@ def profile_query(family: int):
 KERNEL_FAMILIES = {0: "cg_spmm_pq<f32>", 1: "cg_spmm_pq<f64>", 2: "cg_update_xr<f32>",
                    3: "cg_update_xr<f64>", 4: "cg_update_p<f32>", 5: "cg_update_p<f64>",
                    6: "cg_coarse<f32>", 7: "cg_coarse<f64>"}
+
+
+def autotune(on):
+    """True / False: tuning on or off; None: clear the cache (mor_autotune)."""
+    _check(_lib.mor_autotune(-1 if on is None else (1 if on else 0)))
+
+
+def autotune_report():
+    out = np.zeros((64, 8), dtype=np.int64)
+    n = _i32()
+    _check(_lib.mor_autotune_report(_ptr(out), 64, ctypes.byref(n)))
+    names = ["1 record, 256 threads", "2 records, 256 threads", "1 record, 128 threads",
+             "2 records, 128 threads"]
+    return [dict(binary64=bool(r[0]), columns=int(r[1]), slot_width=int(r[2]),
+                 chosen=names[int(r[3])], us=[int(x) for x in r[4:8]])
+            for r in out[:n.value]]
 
 
 def kernel_launches() -> int:

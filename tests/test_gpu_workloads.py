@@ -57,7 +57,8 @@ def _a_orthonormal(V, A):
 
 def _check_sampled(mesh, kappa, owner, p, sd, out, subs, rank_of):
     """Index sets bit-exact; singular values within tol * sigma_1; and the oracle's
-    leading basis [q_0, R_i^{-1} U_m'] inside the span of the GPU's Q_i.  m' <= m is the
+    leading basis [q_0, R_i^{-1} U_m'], projected onto the oracle's kept space, inside
+    the span of the GPU's Q_i.  m' <= m is the
     index of the widest relative gap (sigma_m' - sigma_m'+1) / sigma_1 among the first m:
     by Wedin's theorem the sketched m'-space moves by at most tol / gap', and the GPU's
     m-space contains its m'-space, so the containment residual has that bound too (a gap
@@ -74,7 +75,13 @@ def _check_sampled(mesh, kappa, owner, p, sd, out, subs, rank_of):
         gaps = (ref[:m] - ref[1:m + 1]) / ref[0]
         mp = int(np.argmax(gaps)) + 1
         A = ob["A_PP"]
-        Vo = _a_orthonormal(ob["V"][:, :mp + 1], A)
+        # the leading columns [q_0, R_i^{-1} U_m'] as they lie in the oracle's kept space:
+        # the diagonal-block update drops eigen-directions of V^T A V below
+        # tau * largest, and with k = 1e4 inclusions such a direction can carry part of
+        # q_0 (whose energy norm is 1e-4 of the largest column's), so q_0 itself can lie
+        # outside the kept space by 4e-3; both sides drop it
+        Qo = ob["Q"]
+        Vo = _a_orthonormal(Qo @ (Qo.T @ (A @ ob["V"][:, :mp + 1])), A)
         for prec, tol in (("fp64", 1e-9), ("mixed", 1e-7)):
             b = out[prec][0]
             sig = b.sigma()[i]
