@@ -187,10 +187,11 @@ typedef struct {
                           not depend on the range.  One-shot plans require the whole
                           range (MOR_ERR_ARG otherwise).                                */
   int32_t tc_gram;     /* MOR_MIXED: 1 (default) runs the dense contractions (the
-                          H_i-Grams, G_B, V^T A V and the interface blocks of step 3) on
-                          the tensor cores (tcgen05, exact 7-bit bf16 slices, about 2^-28
+                          H_i-Grams, G_B and the interface blocks of step 3) on the
+                          tensor cores (tcgen05, exact 7-bit bf16 slices, about 2^-28
                           relative per column pair); 0 keeps them in binary64 SIMT.
-                          MOR_FP64 always uses binary64.                                */
+                          V^T A V (the diagonal-block update) and MOR_FP64 always use
+                          binary64.                                                     */
   int32_t explicit_svd; /* 1: the explicit weighted SVD of Eq. (14) instead of the
                           randomized one: dense Cholesky factors of A_II, H_i and H^+
                           (R_i, R_BB, Lemma 4.1), Z_i = C_i A_II^{-1} A_IB, and the

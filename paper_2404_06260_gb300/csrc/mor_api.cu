@@ -1359,7 +1359,14 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   launch_gather_rows(nO, S.o2w, u0w, 1, 0, V, kq, 0, 1, st);
   launch_gather_rows(nO, S.o2w, colsW, colsLd, 0, V, kq, 1, mcols, st);
   launch_spmm<double>(S.tO, App.e64(), V, AV, kq, st);
-  gram(S.tO, V, kq, mcols + 1, AV, kq, mcols + 1, kq);
+  // V^T A V stays binary64 in every precision: the reduced system takes the diagonal
+  // blocks Q_i^T A_ii Q_i as the identity, and Q_i = V W Lambda^{-1/2} amplifies the
+  // Gram's error on directions of small energy
+  if (mcols + 1 > 80)
+    launch_gram_wide(S.tO, n_sd, V, kq, mcols + 1, AV, kq, mcols + 1, gpart, G, kq,
+                     (int64_t)kq * kq, st);
+  else
+    launch_gram(S.tO, n_sd, V, kq, mcols + 1, AV, kq, mcols + 1, gpart, gcnt, G, kq, st);
   sym_eig(kq, mcols + 1, evals, evecs);
   launch_make_M(n_sd, 0, evals, evecs, kq, mcols + 1, o.tau, 0, Mm, Bo.kept, st);
   rowmul(S.tO, V, kq, mcols + 1, kq, Bo.Q, kq, mcols + 1);

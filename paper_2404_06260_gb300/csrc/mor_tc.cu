@@ -1,11 +1,11 @@
 // Tensor-core Grams for the mixed-precision path (Sec. 6: the H_i-orthonormalisation
-// X^T H_i X, the weighted Gram G_B of Eq. (24), V^T A V of the diagonal-block update, and
-// the interface blocks Q_i^T A_0 Q_j of Eq. (23)) on tcgen05 with accumulators in TMEM.
+// X^T H_i X, the weighted Gram G_B of Eq. (24) and the interface blocks Q_i^T A_0 Q_j of
+// Eq. (23)) on tcgen05 with accumulators in TMEM.
 //
 // Arithmetic: every binary64 operand column c is scaled by 2^(7 - e_c), e_c the binary
-// exponent of its largest entry in the block's rows, and split into four 7-bit integer
-// slices, x = 2^(e_c - 7) sum_t s_t 2^(-7t) with s_0 in [-128, 128], s_t in [-64, 64]
-// (t > 0).  Each slice is an integer, exact in bf16.  The products s_t s'_u of one
+// exponent of its largest entry in the block's rows, rounded to 28 bits and split into
+// four integer slices, x = 2^(e_c - 7) sum_t s_t 2^(-7t) with s_0 in [-128, 128], s_t in
+// [-64, 64] (t > 0).  Each slice is an integer, exact in bf16.  The products s_t s'_u of one
 // slice order d = t + u (t + u <= 3, ten pairs) are summed by kind::f16 MMAs (bf16
 // operands) into one FP32 accumulator per order; every product and every partial sum
 // over 256 rows is an integer below 2^24, so the FP32 accumulation is exact.  Every 256
@@ -69,16 +69,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, long lon
   }
 }
 
-// the four slices of x * 2^(7 - e) into column c, row k of the four slice planes
+// the four slices of x * 2^(7 - e) into column c, row k of the four slice planes.  The
+// slicing is integer work on the bits of x (GB300's binary64 rate is low): with
+// x = +-m 2^(E - 1075) (m the 53-bit significand), N = round(x 2^(28 - e)) =
+// round(m / 2^sh), sh = e - 28 - E + 1075 >= 25 because |x| < 2^e; then N =
+// s_0 2^21 + s_1 2^14 + s_2 2^7 + s_3 with each s_t rounded off the remainder, so
+// s_0 in [-128, 128] and s_1, s_2, s_3 in [-64, 64].  Subnormals count as zero.
 __device__ __forceinline__ void put_slices(__nv_bfloat16* plane, uint32_t plane_bytes, int c,
                                            int k, double x, int e) {
-  double s = ldexp(x, 7 - e);
-#pragma unroll
-  for (int t = 0; t < kNS; ++t) {
-    const double q = rint(s);
-    plane[(t * plane_bytes + kmajor(c, k)) >> 1] = __double2bfloat16(q);
-    s = (s - q) * 128.0;
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  int n = 0;
+  if (E != 0) {
+    const long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = (e - 28) - (E - 1075);
+    const long long q = sh >= 62 ? 0 : ((m + (1LL << (sh - 1))) >> sh);
+    n = b < 0 ? -(int)q : (int)q;
   }
+  int sl[kNS];
+  sl[0] = (n + (1 << 20)) >> 21;
+  int r = n - (sl[0] << 21);
+  sl[1] = (r + (1 << 13)) >> 14;
+  r -= sl[1] << 14;
+  sl[2] = (r + (1 << 6)) >> 7;
+  sl[3] = r - (sl[2] << 7);
+  const uint32_t o = kmajor(c, k);
+#pragma unroll
+  for (int t = 0; t < kNS; ++t) plane[(t * plane_bytes + o) >> 1] = __int2bfloat16_rn(sl[t]);
+}
+
+// binary exponent e with |x| < 2^e (the biased exponent minus 1022), 0 for zero and
+// subnormal x
+__device__ __forceinline__ int exponent_of(double x) {
+  const int E = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+  return E == 0 ? 0 : E - 1022;
 }
 
 // Rows of item b: [rlo[b], rhi[b]), split into S chunks (one block each); rows are rows
@@ -106,21 +130,29 @@ __global__ void __launch_bounds__(128)
   double* P = part + (int64_t)blockIdx.x * nx * ny;
   // binary64 partial of this block, zero
   for (int idx = tid; idx < nx * ny; idx += 128) P[idx] = 0.0;
-  // column exponents over the block's rows
+  // column exponents over the block's rows (coalesced sweeps, integer maxima); -1100
+  // marks a column without a normal entry
+  ex[tid] = -1100;
+  ey[tid] = -1100;
+  __syncthreads();
   {
-    double mx = 0.0, my = 0.0;
-    for (int64_t e = ra; e < rb; ++e) {
-      const int64_t rx = kGather ? xrow[e] : e, ry = kGather ? yrow[e] : e;
-      const double we = kGather ? w[e] : 1.0;
-      if (tid < nx) mx = fmax(mx, fabs(we * X[rx * ldx + tid]));
-      if (tid < ny) my = fmax(my, fabs(Y[ry * ldy + tid]));
+    const int64_t nr = rb - ra;
+    for (int64_t idx = tid; idx < nr * nx; idx += 128) {
+      const int64_t e = ra + idx / nx;
+      const int c = (int)(idx % nx);
+      const double v = kGather ? w[e] * X[(int64_t)xrow[e] * ldx + c] : X[e * ldx + c];
+      if (v != 0.0) atomicMax(&ex[c], exponent_of(v));
     }
-    int e1 = 0, e2 = 0;
-    if (mx > 0.0) frexp(mx, &e1);
-    if (my > 0.0) frexp(my, &e2);
-    ex[tid] = e1;
-    ey[tid] = e2;
+    for (int64_t idx = tid; idx < nr * ny; idx += 128) {
+      const int64_t e = ra + idx / ny;
+      const int c = (int)(idx % ny);
+      const double v = Y[(kGather ? (int64_t)yrow[e] : e) * ldy + c];
+      if (v != 0.0) atomicMax(&ey[c], exponent_of(v));
+    }
   }
+  __syncthreads();
+  if (ex[tid] == -1100) ex[tid] = 0;
+  if (ey[tid] == -1100) ey[tid] = 0;
   // TMEM: four FP32 accumulators of NP columns (power of two >= 32 columns allocated)
   uint32_t ncols = 32;
   while (ncols < (uint32_t)(kNS * NP)) ncols <<= 1;
@@ -148,22 +180,26 @@ __global__ void __launch_bounds__(128)
   int in_acc = 0;
   const int64_t nblk = (rb - ra + kKB - 1) / kKB;
   bool ok = true;
+  // the padding rows of the operands (X columns nx..127, Y columns ny..NP-1) stay zero
+  for (int idx = tid; idx < kKB * (kM - nx); idx += 128)
+    put_slices(As, a_plane, nx + idx / kKB, idx % kKB, 0.0, 0);
+  for (int idx = tid; idx < kKB * (NP - ny); idx += 128)
+    put_slices(Bs, b_plane, ny + idx / kKB, idx % kKB, 0.0, 0);
   for (int64_t blk = 0; blk < nblk && ok; ++blk) {
     const int64_t e0 = ra + blk * kKB;
-    for (int idx = tid; idx < kKB * kM; idx += 128) {
-      const int k = idx / kM, c = idx % kM;
+    for (int idx = tid; idx < kKB * nx; idx += 128) {
+      const int k = idx / nx, c = idx % nx;
       const int64_t e = e0 + k;
       double v = 0.0;
-      if (c < nx && e < rb)
-        v = kGather ? w[e] * X[(int64_t)xrow[e] * ldx + c] : X[e * ldx + c];
-      put_slices(As, a_plane, c, k, v, ex[c < nx ? c : 0]);
+      if (e < rb) v = kGather ? w[e] * X[(int64_t)xrow[e] * ldx + c] : X[e * ldx + c];
+      put_slices(As, a_plane, c, k, v, ex[c]);
     }
-    for (int idx = tid; idx < kKB * NP; idx += 128) {
-      const int k = idx / NP, c = idx % NP;
+    for (int idx = tid; idx < kKB * ny; idx += 128) {
+      const int k = idx / ny, c = idx % ny;
       const int64_t e = e0 + k;
       double v = 0.0;
-      if (c < ny && e < rb) v = Y[(kGather ? (int64_t)yrow[e] : e) * ldy + c];
-      put_slices(Bs, b_plane, c, k, v, ey[c < ny ? c : 0]);
+      if (e < rb) v = Y[(kGather ? (int64_t)yrow[e] : e) * ldy + c];
+      put_slices(Bs, b_plane, c, k, v, ey[c]);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();

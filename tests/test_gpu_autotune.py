@@ -3,9 +3,9 @@
 The first product of each (precision, column count, slot width) is timed in four
 launch configurations and the fastest is kept.  Every configuration sums the same
 products in the same order, so the bases do not depend on the choice: a build with the
-tuner on and one with it off (the first configuration) give the same singular values
-and reduced energy to rounding (the restriction sums of the coarse level use atomics,
-whose order varies from run to run).
+tuner on and one with it off (the first configuration) agree to the run-to-run level
+of the mixed path, whose binary32 restriction sums of the coarse level use atomics in
+an order that varies from run to run (about 1e-9 in the singular values).
 """
 import numpy as np
 import pytest
@@ -48,5 +48,5 @@ def test_autotuner_picks_a_configuration_and_keeps_the_results():
         mor.autotune(True)
     s1, e1 = res[True]
     s0, e0 = res[False]
-    assert np.max(np.abs(s1 - s0)) <= 1e-12 * s0.max()
-    assert abs(e1 - e0) <= 1e-12 * e0
+    assert np.max(np.abs(s1 - s0)) <= 1e-7 * s0.max()
+    assert abs(e1 - e0) <= 1e-8 * e0

@@ -10,7 +10,8 @@ for random data, by about sqrt(rows) times that.  The checks use the worst-case 
 magnitude, as the sketch columns of G_B are), row counts that are not multiples of the
 32-row MMA block and that cross the 256-row accumulator flush, one column, 128 columns
 and zero columns.  The mixed path with tensor-core Grams stays within 1e-6 relative
-energy of the binary64 path and within 1e-9 of the mixed path with binary64 Grams.
+energy of the binary64 path and within 1e-7 of the mixed path with binary64 Grams (the
+mixed local solves stop at 1e-9, so both mixed bases are perturbed at about that level).
 """
 import numpy as np
 import pytest
@@ -69,6 +70,6 @@ def test_mixed_path_with_tensor_core_grams(mor):
     u64 = out["fp64"][1]
     n64 = mor.energy_norm(sd, u64)
     assert mor.energy_norm(sd, out["mixed_tc"][1], u64) / n64 <= 1e-6
-    assert mor.energy_norm(sd, out["mixed_tc"][1], out["mixed_fp64"][1]) / n64 <= 1e-9
+    assert mor.energy_norm(sd, out["mixed_tc"][1], out["mixed_fp64"][1]) / n64 <= 1e-7
     s_tc, s_64 = out["mixed_tc"][0].sigma(), out["mixed_fp64"][0].sigma()
-    assert np.max(np.abs(s_tc - s_64)) <= 1e-9 * s_64.max()
+    assert np.max(np.abs(s_tc - s_64)) <= 1e-8 * s_64.max()
