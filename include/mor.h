@@ -186,12 +186,15 @@ typedef struct {
                           check; sub_end <= 0 means all.  The draws of a subdomain do
                           not depend on the range.  One-shot plans require the whole
                           range (MOR_ERR_ARG otherwise).                                */
-  int32_t tc_gram;     /* MOR_MIXED: 1 (default) runs the dense contractions (the
-                          H_i-Grams, G_B and the interface blocks of step 3) on the
-                          tensor cores (tcgen05, exact 7-bit bf16 slices, about 2^-28
-                          relative per column pair); 0 keeps them in binary64 SIMT.
-                          V^T A V (the diagonal-block update) and MOR_FP64 always use
-                          binary64.                                                     */
+  int32_t tc_gram;     /* MOR_MIXED: 1 (default) forms the H_i-Grams and G_B on the
+                          tensor cores (tcgen05, exact 7-bit bf16 slices: entry (i, j)
+                          off by at most about 2^-28 rows max|X_i| max|Y_j|); 2 also
+                          forms the interface blocks of Eq. (23) there, whose error is
+                          then relative to the largest a_e-weighted entry of a column
+                          (at 1e4 coefficient contrast it moves x^T K~ x away from the
+                          lifted energy by about 1e-5 relative); 0 keeps all of them
+                          in binary64 SIMT.  V^T A V (the diagonal-block update) and
+                          MOR_FP64 always use binary64.  Other values: MOR_ERR_ARG.   */
   int32_t explicit_svd; /* 1: the explicit weighted SVD of Eq. (14) instead of the
                           randomized one: dense Cholesky factors of A_II, H_i and H^+
                           (R_i, R_BB, Lemma 4.1), Z_i = C_i A_II^{-1} A_IB, and the

@@ -232,7 +232,7 @@ struct mor_bases_s {
   double* Rbb = nullptr;
   std::vector<int64_t> rbb_off;
   std::vector<int32_t> rbb_m;
-  bool tc = false;  // mixed precision with tensor-core contractions (step 3 follows)
+  bool tc = false;  // tc_gram 2: the interface blocks of step 3 on the tensor cores too
   double *Q = nullptr, *bt = nullptr, *sigma = nullptr;
   int* kept = nullptr;
   std::vector<int32_t> h_kept;
@@ -780,6 +780,8 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   const int n_sd_h = sd->hp.n_sd;
   const bool tol_mode = o.eps > 0.0;
   if (o.sketch_div < 0) return fail(MOR_ERR_ARG, "mor_build_bases: sketch_div must be >= 0");
+  if (o.tc_gram < 0 || o.tc_gram > 2)
+    return fail(MOR_ERR_ARG, "mor_build_bases: tc_gram must be 0, 1 or 2");
   if (o.sketch_div > 0 && (!tol_mode || m_force > 0))
     return fail(MOR_ERR_ARG, "mor_build_bases: sketch_div needs eps > 0 and a one-shot plan");
   std::vector<int32_t> h_rank(n_sd_h), h_k(n_sd_h);
@@ -1390,7 +1392,7 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
     if (h_tcerr)
       return fail(MOR_ERR_TIMEOUT, "mor_build_bases: a tensor-core Gram's wait ran out of its "
                                    "budget (mor_set_wait_budget)");
-    Bo.tc = true;
+    Bo.tc = o.tc_gram >= 2;
   }
   Bo.h_kept.resize(n_sd);
   Bo.h_sigma.resize((size_t)n_sd * Bo.kp);
