@@ -169,7 +169,7 @@ typedef struct {
   int32_t coarse_rows; /* local preconditioner: > 0 adds a coarse level to Jacobi,
                           M^{-1} = D^{-1} + Z E^{-1} Z^T with Z the indicators of
                           spatial aggregates of about coarse_rows rows (runs of the
-                          Morton-ordered rows of a subdomain, at most 256 per
+                          Morton-ordered rows of a subdomain, at most 1024 per
                           subdomain) and E = Z^T A Z inverted per subdomain; 0: Jacobi
                           only.  Changes iteration counts, not the solutions.         */
   int32_t h1_weighted; /* 0: the H1 inner product of H_i and H^+ is the unweighted
@@ -205,7 +205,7 @@ typedef struct {
 
 /* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
  * max_iter 20000, replace_every 40, normwise 1, drift_restart 1.5, sketch_rtol 0,
- * tau 1e-12, orth_tol 1e-14, coarse_rows 100, h1_weighted 0, sketch_div 0, sub_begin 0,
+ * tau 1e-12, orth_tol 1e-14, coarse_rows 35, h1_weighted 0, sketch_div 0, sub_begin 0,
  * sub_end 0, tc_gram 1, explicit_svd 0). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 
@@ -369,6 +369,15 @@ int mor_debug_sketch_rhs(const mor_subdomains* sd, const mor_basis_opts* opts,
  * binary64). */
 int mor_debug_tc_gram(int64_t rows, int32_t nx, int32_t ny, const double* X_dev,
                       const double* Y_dev, double* G_dev, void* stream);
+
+/* Debug/parity access: the inverse that the coarse level of the local preconditioner
+ * takes of every aggregate matrix E = Z^T A Z (mor_basis_opts.coarse_rows): blocked
+ * Gauss-Jordan elimination without pivoting on diag(E)^{-1/2} E diag(E)^{-1/2} in
+ * binary32, symmetrised.  E_dev [device, n x n] symmetric positive definite binary64,
+ * 1 <= n <= 1024; Einv_dev [device, n x n] is written.  MOR_ERR_ARG on a non-positive
+ * diagonal entry or pivot.  Allocates its work space.  The paper has no counterpart (its
+ * local solves are direct). */
+int mor_debug_coarse_inverse(int32_t n, const double* E_dev, double* Einv_dev, void* stream);
 
 /* Kernel timing for the roofline: when enabled, the four kernels of every local CG
  * step of mor_build_bases are bracketed by CUDA events on the launching stream.

@@ -504,7 +504,7 @@ int mor_basis_opts_default(mor_basis_opts* o) {
   o->sketch_rtol = 0.0;
   o->tau = 1e-12;
   o->orth_tol = 1e-14;
-  o->coarse_rows = 100;
+  o->coarse_rows = 35;
   o->h1_weighted = 0;
   o->sketch_div = 0;
   o->tc_gram = 1;
@@ -925,44 +925,69 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
     TRY(M.alloc((unsigned char**)&yc, (size_t)n_agg * kp * tsz_c, true, st));
     int* d_bad;
     TRY(M.alloc(&d_bad, 1, true, st));
+    // E (binary64, assembled) and the inversion workspace, shared by both matrices
+    int n_max[2] = {1, 1};
+    int64_t ne_max = 1;
     for (int set = 0; set < 2; ++set) {
-      const DTiles& tl = set == 0 ? S.tP_I : S.tP_all;
-      const Mat& Am = set == 0 ? A_II : Hp;
-      int32_t *nca, *tfirst, *tcount;
-      int64_t *toff, *eoff;
-      TRY(M.upload(&nca, ap.nca[set], st));
-      TRY(M.upload(&tfirst, ap.tfirst[set], st));
-      TRY(M.upload(&tcount, ap.tcount[set], st));
-      TRY(M.upload(&toff, ap.toff[set], st));
-      TRY(M.upload(&eoff, ap.eoff[set], st));
-      const int64_t ne = ap.eoff[set][n_sd];
-      double* E;
-      TRY(M.alloc(&E, std::max<int64_t>(ne, 1), true, st));
-      void *einv, *cpart;
-      TRY(M.alloc((unsigned char**)&einv, (size_t)std::max<int64_t>(ne, 1) * tsz_c, true, st));
-      TRY(M.alloc((unsigned char**)&cpart, (size_t)std::max<int64_t>(ap.toff[set].back(), 1) *
-                                               kp * tsz_c, true, st));
-      launch_coarse_matrix(tl, Am.e64(), aloc, nca, eoff, E, st);
-      if (B.mixed)
-        launch_coarse_invert<float>(n_sd, nca, eoff, E, (float*)einv, d_bad, st);
-      else
-        launch_coarse_invert<double>(n_sd, nca, eoff, E, (double*)einv, d_bad, st);
-      auto fill = [&](auto& c, auto* ei, auto* cp, auto* y) {
-        c.aloc = aloc;
-        c.aoff = aoff;
-        c.nca = nca;
-        c.tfirst = tfirst;
-        c.tcount = tcount;
-        c.toff = toff;
-        c.eoff = eoff;
-        c.einv = ei;
-        c.cpart = cp;
-        c.yc = y;
-      };
-      if (B.mixed)
-        fill(B.co32[set], (const float*)einv, (float*)cpart, (float*)yc);
-      else
-        fill(B.co64[set], (const double*)einv, (double*)cpart, (double*)yc);
+      for (int i = 0; i < n_sd; ++i) n_max[set] = std::max(n_max[set], ap.nca[set][i]);
+      ne_max = std::max<int64_t>(ne_max, ap.eoff[set][n_sd]);
+    }
+    const int nm = std::max(n_max[0], n_max[1]);
+    double *E, *sc;
+    float *W, *P;
+    {
+      Allocs Wk;  // released after the inversions
+      Wk.use_pool(st);
+      TRY(Wk.alloc(&E, ne_max, false, st));
+      TRY(Wk.alloc(&W, ne_max, false, st));
+      TRY(Wk.alloc(&P, (size_t)n_sd * kCoarsePivots * kCoarsePivots, false, st));
+      TRY(Wk.alloc(&sc, (size_t)n_sd * nm, false, st));
+      for (int set = 0; set < 2; ++set) {
+        const DTiles& tl = set == 0 ? S.tP_I : S.tP_all;
+        const Mat& Am = set == 0 ? A_II : Hp;
+        int32_t *nca, *tfirst, *tcount;
+        int64_t *toff, *eoff;
+        TRY(M.upload(&nca, ap.nca[set], st));
+        TRY(M.upload(&tfirst, ap.tfirst[set], st));
+        TRY(M.upload(&tcount, ap.tcount[set], st));
+        TRY(M.upload(&toff, ap.toff[set], st));
+        TRY(M.upload(&eoff, ap.eoff[set], st));
+        const int64_t ne = ap.eoff[set][n_sd];
+        const int nrb = (n_max[set] + kCoarseRows - 1) / kCoarseRows;
+        void *einv, *cpart;
+        double* dpart;
+        TRY(M.alloc((unsigned char**)&einv, (size_t)std::max<int64_t>(ne, 1) * tsz_c, true, st));
+        TRY(M.alloc((unsigned char**)&cpart, (size_t)std::max<int64_t>(ap.toff[set].back(), 1) *
+                                                 kp * tsz_c, true, st));
+        TRY(M.alloc(&dpart, (size_t)n_sd * nrb * kp, true, st));
+        CK(cudaMemsetAsync(E, 0, sizeof(double) * std::max<int64_t>(ne, 1), st));
+        launch_coarse_matrix(tl, Am.e64(), aloc, nca, eoff, E, st);
+        if (B.mixed)
+          launch_coarse_invert<float>(n_sd, n_max[set], nca, eoff, E, W, P, sc, (float*)einv,
+                                      d_bad, st);
+        else
+          launch_coarse_invert<double>(n_sd, n_max[set], nca, eoff, E, W, P, sc,
+                                       (double*)einv, d_bad, st);
+        auto fill = [&](auto& c, auto* ei, auto* cp, auto* y) {
+          c.aloc = aloc;
+          c.aoff = aoff;
+          c.nca = nca;
+          c.tfirst = tfirst;
+          c.tcount = tcount;
+          c.toff = toff;
+          c.eoff = eoff;
+          c.einv = ei;
+          c.cpart = cp;
+          c.yc = y;
+          c.dpart = dpart;
+          c.n_max = n_max[set];
+        };
+        if (B.mixed)
+          fill(B.co32[set], (const float*)einv, (float*)cpart, (float*)yc);
+        else
+          fill(B.co64[set], (const double*)einv, (double*)cpart, (double*)yc);
+      }
+      CK(cudaStreamSynchronize(st));
     }
     int h_bad = 0;
     CK(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1918,6 +1943,36 @@ int mor_debug_tc_gram(int64_t rows, int32_t nx, int32_t ny, const double* X_dev,
   CK(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (h) return fail(MOR_ERR_TIMEOUT, "mor_debug_tc_gram: a wait ran out of its budget");
+  return MOR_OK;
+}
+
+int mor_debug_coarse_inverse(int32_t n, const double* E_dev, double* Einv_dev, void* stream) {
+  if (n < 1 || n > kMaxAgg || !E_dev || !Einv_dev)
+    return fail(MOR_ERR_ARG, "mor_debug_coarse_inverse: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Allocs A;
+  A.use_pool(st);
+  int32_t* nca;
+  int64_t* eoff;
+  float *W, *P;
+  double* sc;
+  int* bad;
+  const int32_t h_n = n;
+  const int64_t h_off = 0;
+  TRY(A.alloc(&nca, 1, false, st));
+  TRY(A.alloc(&eoff, 1, false, st));
+  TRY(A.alloc(&W, (size_t)n * n, false, st));
+  TRY(A.alloc(&P, (size_t)kCoarsePivots * kCoarsePivots, false, st));
+  TRY(A.alloc(&sc, (size_t)n, false, st));
+  TRY(A.alloc(&bad, 1, true, st));
+  CK(cudaMemcpyAsync(nca, &h_n, sizeof h_n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(eoff, &h_off, sizeof h_off, cudaMemcpyHostToDevice, st));
+  launch_coarse_invert<double>(1, n, nca, eoff, E_dev, W, P, sc, Einv_dev, bad, st);
+  int h = 0;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h) return fail(MOR_ERR_ARG, "mor_debug_coarse_inverse: a pivot is not positive");
   return MOR_OK;
 }
 

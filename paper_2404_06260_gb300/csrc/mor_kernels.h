@@ -101,7 +101,8 @@ struct CgState {
 // E = Z^T A Z per subdomain, inverted once per matrix.  With aloc = null the
 // preconditioner is D^{-1} alone.
 constexpr int kMaxSlots = 32;  // aggregates meeting one row tile (host-enforced)
-constexpr int kMaxAgg = 256;   // aggregates per subdomain and matrix (host-enforced)
+constexpr int kMaxAgg = 1024;  // aggregates per subdomain and matrix (host-enforced)
+constexpr int kCoarseRows = 512;  // rows of E^{-1} per block of the coarse product
 template <typename T>
 struct Coarse {
   const int32_t* aloc = nullptr;    // per P row: aggregate index within its subdomain
@@ -114,6 +115,8 @@ struct Coarse {
   const T* einv = nullptr;          // E^{-1} blocks, symmetric, row-major
   T* cpart = nullptr;               // toff[n_tiles] x kp restriction partials
   T* yc = nullptr;                  // global aggregates x kp: E^{-1} Z^T r
+  double* dpart = nullptr;          // n_sd x row blocks x kp: partial r_c . y_c
+  int n_max = 0;                    // largest nca
 };
 
 template <typename T>
@@ -193,11 +196,15 @@ void launch_cg_replace(const DTiles& tiles, const double* r64, T* rT, T* pT, con
 // b = aloc[j] (entries with a or b >= nca[sd] are skipped); E zeroed by the caller.
 void launch_coarse_matrix(const DTiles& tiles, const EllView<double>& A, const int32_t* aloc,
                           const int32_t* nca, const int64_t* eoff, double* E, cudaStream_t st);
-// In-place Gauss-Jordan inverse of every SPD block E[sd] (binary64, no pivoting), then
-// einv = (E^{-1} + E^{-T}) / 2 in T.  bad[0] counts blocks with a non-positive pivot.
+// einv = E^{-1} of every SPD block E[sd] (nca[sd] <= n_max), symmetrised, in T: blocked
+// Gauss-Jordan elimination without pivoting on the diagonally scaled block in binary32.
+// Workspace: W [eoff[n_sd] floats], P [n_sd x 64 x 64 floats], sc [n_sd x n_max
+// doubles].  bad[0] counts blocks with a non-positive diagonal entry or pivot.
 template <typename T>
-void launch_coarse_invert(int n_sd, const int32_t* nca, const int64_t* eoff, double* E,
-                          T* einv, int* bad, cudaStream_t st);
+void launch_coarse_invert(int n_sd, int n_max, const int32_t* nca, const int64_t* eoff,
+                          const double* E, float* W, float* P, double* sc, T* einv, int* bad,
+                          cudaStream_t st);
+constexpr int kCoarsePivots = 64;  // pivot block of launch_coarse_invert
 // x64 += xT, xT = 0
 template <typename T>
 void launch_accum_reset(const DTiles& tiles, T* xT, double* x64, int kp, cudaStream_t st);

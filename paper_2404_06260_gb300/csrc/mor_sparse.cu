@@ -9,6 +9,7 @@
 // reductions are deterministic and need no extra launch.
 #include "mor_kernels.h"
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 #include "mor_plan.h"
@@ -662,111 +663,165 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4)
   }
 }
 
-// Coarse level of one subdomain and a chunk of kCoarseCols columns (grid n_sd x chunks):
-// r_c = Z^T r from the tile partials, y_c = E^{-1} r_c (stored for the p update), and
-// r.M^{-1}r = fine part + r_c.y_c.  mode STEP: the convergence test on the recursive
-// residual and beta = (r.z)_new / (r.z)_old; INIT / REPLACE: rz only (beta and gam come
-// from the init / replacement kernel).  Without a coarse level y_c = 0.
+// Coarse level of one subdomain (grid: x = row block x column chunk, y = subdomain).
+// Block (rb, chunk) forms r_c = Z^T r for the chunk's kCoarseCols columns from the tile
+// partials, then rows [rb kCoarseRows, (rb + 1) kCoarseRows) of y_c = E^{-1} r_c (stored
+// for the p update), kCoarseRpt rows per thread, and their part of r_c.y_c.  The last block of
+// the subdomain (atomic ticket) adds the parts in row-block order, r.M^{-1}r = fine part
+// + r_c.y_c, and in mode STEP takes the convergence test on the recursive residual and
+// beta = (r.z)_new / (r.z)_old; INIT / REPLACE: rz only (beta and gam come from the init
+// / replacement kernel).  Without a coarse level y_c = 0.  The blocks of one row block
+// are adjacent in the grid, so the chunks read its E^{-1} rows from L2 after the first.
 constexpr int kCoarseCols = 16;
+constexpr int kCoarseRpt = 2;  // rows of y_c per thread
+constexpr int kCoarseThreads = kCoarseRows / kCoarseRpt;
+constexpr size_t kCoarseRedBytes = sizeof(double) * (kCoarseThreads / 32) * kCoarseCols;
 enum { kCoarseInit = 0, kCoarseStep = 1, kCoarseReplace = 2 };
 template <typename T>
-__global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s, Coarse<T> co) {
+__global__ void __launch_bounds__(kCoarseThreads)
+    k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s, Coarse<T> co) {
   constexpr int CW = kCoarseCols;
+  constexpr int PN = Pack<T>::N;
   Geo g = geo();
   extern __shared__ __align__(16) unsigned char raw[];
-  T* rc = reinterpret_cast<T*>(raw);  // n x CW
-  double* red = reinterpret_cast<double*>(raw + align16(sizeof(T) * kMaxAgg * CW));
-  __shared__ double cd[CW];
-  const int sd = blockIdx.x, c0 = blockIdx.y * CW;
+  T* rc = reinterpret_cast<T*>(raw);  // round_up(n, 8) x CW
+  // rc holds round_up(n_max, 8) rows (the product reads whole groups of 8)
+  const int n_max8 = co.aloc ? (co.n_max + 7) & ~7 : 0;
+  double* red = reinterpret_cast<double*>(raw + align16(sizeof(T) * n_max8 * CW));
+  const int sd = blockIdx.y;
+  const int nchunk = (kp + CW - 1) / CW;
+  const int chunk = blockIdx.x % nchunk, rbk = blockIdx.x / nchunk;
+  const int nrb = gridDim.x / nchunk;
+  const int c0 = chunk * CW, ncol = min(CW, kp - c0);
+  const int cw = CW;
   if (s.active[sd] == 0) return;
   // a chunk whose columns have all converged needs no coarse product
   bool chunk_open = false;
-  for (int j = 0; j < CW && c0 + j < kp; ++j) chunk_open = chunk_open || !s.done[sd * kp + c0 + j];
+  for (int j = 0; j < ncol; ++j) chunk_open = chunk_open || !s.done[sd * kp + c0 + j];
   const int n = (co.aloc && chunk_open) ? co.nca[sd] : 0;
-  // open packs of this chunk before the update (the sparse product and the x/r update
-  // of this step worked on them)
-  constexpr int PN = Pack<T>::N;
-  int open_pre = 0;
-  if (s.work && mode == kCoarseStep && g.tid == 0)
-    for (int j = 0; j < CW && c0 + j < kp; j += PN) {
-      bool open = false;
-      for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + c0 + j + e];
-      open_pre += open;
-    }
-  const int a0 = n ? co.aoff[sd] : 0;
-  // r_c = Z^T r: thread a sums the partial rows of aggregate a over the tiles holding
-  // it (contiguous 16-byte packs of this column chunk; kp and c0 are multiples of the
-  // pack width).  Rows n .. round_up(n, 8) are zero: the product below runs in steps
-  // of 8.
-  const int n8 = (n + 7) & ~7;
-  for (int a = g.tid; a < n8; a += g.nth) {
-    T v[CW];
-#pragma unroll
-    for (int j = 0; j < CW; ++j) v[j] = T(0);
-    if (a < n) {
-      const int ga = a0 + a;
-      const int t0 = co.tfirst[ga], tn = co.tcount[ga];
-      for (int t = t0; t < t0 + tn; ++t) {
-        const int slot = a - co.aloc[tl.r0[t]];
-        const T* src = co.cpart + (co.toff[t] + slot) * kp + c0;
-#pragma unroll
-        for (int j = 0; j < CW; j += PN)
-          if (c0 + j < kp) {
-            Pack<T> pv = ld(src + j);
-#pragma unroll
-            for (int e = 0; e < PN; ++e) v[j + e] += pv.v[e];
-          }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < CW; ++j) rc[a * CW + j] = v[j];
-  }
-  __syncthreads();
+  const int a_lo = rbk * kCoarseRows, a_hi = min(n, a_lo + kCoarseRows);
   double dl[CW];
 #pragma unroll
   for (int j = 0; j < CW; ++j) dl[j] = 0.0;
-  if (n > 0) {
-    const T* Eb = co.einv + co.eoff[sd];
-    for (int a = g.tid; a < n; a += g.nth) {
-      T acc[CW];
+  if (a_lo < n) {
+    const int a0 = co.aoff[sd];
+    // r_c = Z^T r: one (aggregate, pack) pair per thread step, summed over the tiles
+    // holding the aggregate (kp and c0 are multiples of the pack width).  Rows
+    // n .. round_up(n, 8) are zero: the product runs in steps of 8.
+    const int n8 = (n + 7) & ~7, cwp = CW / PN;
+    for (int idx = g.tid; idx < n8 * cwp; idx += g.nth) {
+      const int a = idx / cwp, pk = idx - a * cwp;
+      Pack<T> v;
 #pragma unroll
-      for (int j = 0; j < CW; ++j) acc[j] = T(0);
-      // E^{-1} is symmetric: thread a reads column a (coalesced across threads); eight
+      for (int e = 0; e < PN; ++e) v.v[e] = T(0);
+      if (a < n && pk * PN < ncol) {
+        const int ga = a0 + a;
+        const int t0 = co.tfirst[ga], tn = co.tcount[ga];
+        for (int t = t0; t < t0 + tn; ++t) {
+          const int slot = a - co.aloc[tl.r0[t]];
+          Pack<T> pv = ld(co.cpart + (co.toff[t] + slot) * kp + c0 + pk * PN);
+#pragma unroll
+          for (int e = 0; e < PN; ++e) v.v[e] += pv.v[e];
+        }
+      }
+      st(rc + a * CW + pk * PN, v);
+    }
+    __syncthreads();
+    // rows a_lo + tid + kCoarseThreads i, i < kCoarseRpt, one thread each
+    if (a_lo + g.tid < a_hi) {
+      // E^{-1} is symmetric: row a is read as column a, coalesced across the block;
+      // each element feeds the CW multiply-adds of the chunk, the r_c pieces (broadcast
+      // shared loads) feed the kCoarseRpt rows of the thread, and eight columns of
       // loads are issued before their multiply-adds
+      const T* Eb = co.einv + co.eoff[sd];
+      int ra[kCoarseRpt];
+      bool rv[kCoarseRpt];
+#pragma unroll
+      for (int i = 0; i < kCoarseRpt; ++i) {
+        ra[i] = a_lo + g.tid + kCoarseThreads * i;
+        rv[i] = ra[i] < a_hi;
+      }
+      T acc[kCoarseRpt][CW];
+#pragma unroll
+      for (int i = 0; i < kCoarseRpt; ++i)
+#pragma unroll
+        for (int j = 0; j < CW; ++j) acc[i][j] = T(0);
       for (int b0 = 0; b0 < n; b0 += 8) {
-        T e[8];
+        T e[8][kCoarseRpt];
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-          e[u] = (b0 + u < n) ? Eb[(int64_t)(b0 + u) * n + a] : T(0);
+#pragma unroll
+          for (int i = 0; i < kCoarseRpt; ++i)
+            e[u][i] = (b0 + u < n && rv[i]) ? Eb[(int64_t)(b0 + u) * n + ra[i]] : T(0);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const T* rb = rc + (b0 + u) * CW;
 #pragma unroll
-          for (int j = 0; j < CW; ++j) acc[j] += e[u] * rb[j];
+          for (int h = 0; h < CW; h += PN) {
+            Pack<T> xv = ld(rb + h);
+#pragma unroll
+            for (int i = 0; i < kCoarseRpt; ++i)
+#pragma unroll
+              for (int e2 = 0; e2 < PN; ++e2) acc[i][h + e2] += e[u][i] * xv.v[e2];
+          }
         }
       }
-      T* yo = co.yc + (int64_t)(a0 + a) * kp + c0;
 #pragma unroll
-      for (int j = 0; j < CW; ++j) {
-        if (c0 + j < kp) yo[j] = acc[j];
-        dl[j] += (double)acc[j] * (double)rc[a * CW + j];
+      for (int i = 0; i < kCoarseRpt; ++i) {
+        if (!rv[i]) continue;
+        T* yo = co.yc + (int64_t)(a0 + ra[i]) * kp + c0;
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+          if (j < ncol) yo[j] = acc[i][j];
+          dl[j] += (double)acc[i][j] * (double)rc[ra[i] * CW + j];
+        }
       }
     }
   }
+  // this block's part of r_c.y_c per column: rows summed within each warp (fixed
+  // shuffle tree), then the warps in order
+  {
+    const int lane = g.tid & 31, wid = g.tid >> 5;
 #pragma unroll
-  for (int j = 0; j < CW; ++j) red[g.tid * CW + j] = dl[j];
+    for (int j = 0; j < CW; ++j) {
+      double v = dl[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[wid * CW + j] = v;
+    }
+    __syncthreads();
+    if (g.tid < ncol && co.dpart) {
+      double t = 0.0;
+      for (int w = 0; w < g.nth / 32; ++w) t += red[w * CW + g.tid];
+      co.dpart[((int64_t)sd * nrb + rbk) * kp + c0 + g.tid] = t;
+    }
+  }
+  if (!last_block(g, s.counter, sd, gridDim.x)) return;
+  // the subdomain's columns: open packs before the update (the sparse product and the
+  // x/r update of this step worked on them), the test and beta, open packs after
+  __shared__ int open_pre, open_post, chunks_open;
+  const bool count = s.work && mode == kCoarseStep;
+  if (g.tid == 0) open_pre = open_post = chunks_open = 0;
   __syncthreads();
-  if (g.tid < CW) {
-    double t = 0.0;
-    for (int q = 0; q < g.nth; ++q) t += red[q * CW + g.tid];  // fixed order
-    cd[g.tid] = t;
+  if (count) {
+    for (int pk = g.tid; pk * PN < kp; pk += g.nth) {
+      bool open = false;
+      for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + pk * PN + e];
+      if (open) atomicAdd(&open_pre, 1);
+    }
+    for (int ch = g.tid; ch < nchunk; ch += g.nth) {
+      bool open = false;
+      for (int j = 0; j < cw && ch * cw + j < kp; ++j) open = open || !s.done[sd * kp + ch * cw + j];
+      if (open) atomicAdd(&chunks_open, 1);
+    }
   }
   __syncthreads();
-  for (int j = g.tid; j < CW; j += g.nth) {
-    int c = c0 + j;
-    if (c >= kp) continue;
-    int i = sd * kp + c;
-    double rzn = s.rzf[i] + cd[j];
+  for (int c = g.tid; c < kp; c += g.nth) {
+    const int i = sd * kp + c;
+    double cd = 0.0;
+    if (co.dpart)
+      for (int r = 0; r < nrb; ++r) cd += __ldcg(co.dpart + ((int64_t)sd * nrb + r) * kp + c);
+    const double rzn = s.rzf[i] + cd;
     if (mode == kCoarseStep) {
       double be = 0.0;
       if (!s.done[i]) {
@@ -784,25 +839,25 @@ __global__ void k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s,
     }
   }
   if (mode != kCoarseStep) return;
-  if (s.work) {
+  __syncthreads();
+  if (count) {
+    for (int pk = g.tid; pk * PN < kp; pk += g.nth) {
+      bool open = false;
+      for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + pk * PN + e];
+      if (open) atomicAdd(&open_post, 1);
+    }
     __syncthreads();
     if (g.tid == 0) {
-      // open packs after the update (the p update works on them), and the work counts
-      int open_post = 0;
-      for (int j = 0; j < CW && c0 + j < kp; j += PN) {
-        bool open = false;
-        for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + c0 + j + e];
-        open_post += open;
-      }
+      // work counts of the algorithmic-bytes model
       const int nsd = tl.n_sd;
       const unsigned long long rows = (unsigned long long)s.sd_rows[sd];
-      if (blockIdx.y == 0) atomicAdd(s.work + sd, (unsigned long long)s.sd_nnz[sd]);
+      const unsigned long long nc = co.aloc ? (unsigned long long)co.nca[sd] : 0ull;
+      atomicAdd(s.work + sd, (unsigned long long)s.sd_nnz[sd]);
       atomicAdd(s.work + nsd + sd, (unsigned long long)open_pre * rows);
       atomicAdd(s.work + 2 * nsd + sd, (unsigned long long)open_post * rows);
-      if (n > 0) atomicAdd(s.work + 3 * nsd + sd, (unsigned long long)n * n);
+      if (nc) atomicAdd(s.work + 3 * nsd + sd, (unsigned long long)chunks_open * nc * nc);
     }
   }
-  if (!last_block(g, s.counter, sd, gridDim.y)) return;
   count_active(g, s.done, sd, kp, s.active);
   if (g.tid == 0 && s.active[sd] > 0) s.iters[sd] += 1;
 }
@@ -1035,16 +1090,18 @@ void launch_coarse_then_p(const DTiles& tiles, int n_sd, const T* r, T* p, const
                           cudaStream_t st, const cudaEvent_t* ev_mid) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute((const void*)k_cg_coarse<T>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute((const void*)k_cg_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(align16(sizeof(T) * kMaxAgg * kCoarseCols) + kCoarseRedBytes));
     attr = true;
   }
-  const int nthr = 256;
-  size_t sm = align16(sizeof(T) * kMaxAgg * kCoarseCols) + sizeof(double) * nthr * kCoarseCols;
-  dim3 grid(n_sd, (kp + kCoarseCols - 1) / kCoarseCols);
+  const int n_max = co.aloc ? co.n_max : 0;
+  const size_t sm = align16(sizeof(T) * ((n_max + 7) & ~7) * kCoarseCols) + kCoarseRedBytes;
+  const int nrb = std::max(1, (n_max + kCoarseRows - 1) / kCoarseRows);
+  const int nchunk = (kp + kCoarseCols - 1) / kCoarseCols;
+  dim3 grid(nrb * nchunk, n_sd);
   dim3 bl = block_of<T>(kp);
   count_launch(2);
-  k_cg_coarse<T><<<grid, nthr, sm, st>>>(tiles, kp, tol2, mode, s, co);
+  k_cg_coarse<T><<<grid, kCoarseThreads, sm, st>>>(tiles, kp, tol2, mode, s, co);
   if (ev_mid) cudaEventRecord(*ev_mid, st);
   k_cg_update_p<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, r, p, dinv,
                                                                          kp, s, co);

@@ -91,6 +91,7 @@ _sig("mor_set_wait_budget", _i32, _dbl)
 _sig("mor_debug_wait_timeout", _i32, _dbl, ctypes.POINTER(_i32))
 _sig("mor_energy_norm", _i32, _P, _P, _P, ctypes.POINTER(_dbl), _P)
 _sig("mor_debug_tc_gram", _i32, _i64, _i32, _i32, _P, _P, _P, _P)
+_sig("mor_debug_coarse_inverse", _i32, _i32, _P, _P, _P)
 _sig("mor_debug_sketch_rhs", _i32, _P, ctypes.POINTER(BasisOpts), _i32, _P, _P)
 _sig("mor_profile_enable", _i32, _i32)
 _sig("mor_profile_reset", _i32)
@@ -112,7 +113,7 @@ EXPORTED = ["mor_build_subdomains", "mor_build_subdomains_host",
             "mor_solve_reduced_noalloc", "mor_set_wait_budget", "mor_debug_wait_timeout",
             "mor_lift",
             "mor_energy_norm", "mor_debug_sketch_rhs", "mor_debug_plan_check",
-            "mor_debug_tc_gram",
+            "mor_debug_tc_gram", "mor_debug_coarse_inverse",
             "mor_profile_enable",
             "mor_profile_reset", "mor_profile_query", "mor_kernel_launches", "mor_autotune",
             "mor_autotune_report", "mor_free_subdomains",
@@ -396,6 +397,17 @@ def tc_gram(X, Y, stream=None):
     return G
 
 
+def coarse_inverse(E, stream=None):
+    """The coarse level's inverse of an SPD aggregate matrix (mor_debug_coarse_inverse);
+    E a binary64 CUDA tensor n x n."""
+    assert E.is_cuda and E.dtype == torch.float64 and E.shape[0] == E.shape[1]
+    E = E.contiguous()
+    out = torch.empty_like(E)
+    _check(_lib.mor_debug_coarse_inverse(int(E.shape[0]), _P(E.data_ptr()), _P(out.data_ptr()),
+                                         _stream(stream)))
+    return out
+
+
 def profile(on: bool):
     _check(_lib.mor_profile_enable(1 if on else 0))
 
@@ -437,7 +449,7 @@ def kernel_launches() -> int:
     return out.value
 
 
-def plan_check(mesh, owner, r_hops: int, wave: int, coarse_rows: int = 100) -> dict:
+def plan_check(mesh, owner, r_hops: int, wave: int, coarse_rows: int = 35) -> dict:
     """Host-only consistency check of step 1 (mor_debug_plan_check); needs no GPU."""
     tets = np.ascontiguousarray(mesh.tets, dtype=np.int32)
     dirichlet = np.ascontiguousarray(mesh.dirichlet, dtype=np.uint8)

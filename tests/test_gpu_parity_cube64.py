@@ -4,8 +4,8 @@ cg_rtol 1e-9) and in binary64.
 
 The oracle computes sampled outputs one subdomain at a time: subdomain 0, the corner
 box (|I| = 12,167), takes about 15 s on the CPU, and subdomain 21, an interior box
-with the largest extension (|I| = 27,080, the size that meets the 256-aggregate cap of
-the coarse level), about 40 s.  Sampled outputs: singular values, subspaces and the
+with the largest extension (|I| = 27,080, the subdomain with the most coarse-level
+aggregates), about 40 s.  Sampled outputs: singular values, subspaces and the
 rotation-invariant projected load Q_i b~_i of subdomains 0 and 21, and the
 rotation-invariant interface blocks Q_i K~_ij Q_j^T of the neighbour pairs (0, 1) and
 (21, 22).  Every subdomain's index sets and the sketch right-hand side of sampled
