@@ -27,11 +27,25 @@ void parallel_for(int n, int n_threads, F f) {
   for (auto& x : th) x.join();
 }
 
+// Rows of one local space (rows numbered by their local index): the sorted local
+// columns of every row (nodes sharing an element of `elems` with it) and its incidence
+// entries (the elements of `elems` holding the row's node, ascending).  Element-driven:
+// every element's four local vertex indices are looked up once into W.evl, the
+// (element, vertex) pairs are bucketed by row in element order, and each row then
+// reads only the small table.  W holds the work arrays (reused across calls).
+struct RowWork {
+  std::vector<int32_t> evl;    // 4 per element: local index of each vertex, or -1
+  std::vector<int64_t> start;  // per row: first (element, vertex) pair
+  std::vector<int64_t> fill;
+  std::vector<int32_t> pairs;  // 4 * element position + vertex slot, bucketed by row
+  std::vector<int32_t> seen, slot_of, cand;
+};
+
 // per-thread scratch, stamped with subdomain id + 1 so it never needs clearing
 struct Scratch {
   std::vector<int32_t> ball, vert, loc_mark, loc, wmark, wloc;
   std::vector<uint8_t> tplus, tomega;
-  std::vector<int32_t> seen, slot_of;  // build_rows work arrays
+  RowWork rows;  // build_rows work arrays
   void init(int64_t n_nodes, int64_t n_tets) {
     ball.assign(n_nodes, 0);
     vert.assign(n_nodes, 0);
@@ -78,53 +92,65 @@ void sort_flagged(std::vector<int32_t>& ids, const std::vector<uint8_t>& flag) {
   }
 }
 
-// Rows of one local space (row_nodes in local order): the sorted local columns of every
-// row (nodes sharing an element of tflag with it) and its incidence entries.  seen and
-// slot_of are work arrays over the local indices: seen dedupes a row's candidates
-// (stamped with a per-call row counter), slot_of maps a local column to its slot.
-void build_rows(const std::vector<int32_t>& row_nodes, const int32_t* tets,
-                const std::vector<int64_t>& n2t_ptr, const std::vector<int32_t>& n2t,
-                const std::vector<uint8_t>& tflag, const std::vector<int32_t>& mark,
-                const std::vector<int32_t>& loc, int32_t stamp, LocalRows& R,
-                std::vector<int32_t>& seen, std::vector<int32_t>& slot_of) {
-  seen.assign(row_nodes.size(), -1);
-  if (slot_of.size() < row_nodes.size()) slot_of.resize(row_nodes.size());
-  std::vector<int32_t> cand;
-  int32_t row = 0;
-  for (int32_t g : row_nodes) {
+void build_rows(int64_t n_rows, const std::vector<int32_t>& elems, const int32_t* tets,
+                const std::vector<int32_t>& mark, const std::vector<int32_t>& loc,
+                int32_t stamp, LocalRows& R, RowWork& W) {
+  const int64_t ne = (int64_t)elems.size();
+  W.evl.resize(4 * ne);
+  W.start.assign(n_rows + 1, 0);
+  for (int64_t p = 0; p < ne; ++p) {
+    const int32_t* t = tets + 4 * (int64_t)elems[p];
+    for (int b = 0; b < 4; ++b) {
+      const int32_t vb = t[b];
+      const int32_t l = mark[vb] == stamp ? loc[vb] : -1;
+      W.evl[4 * p + b] = l;
+      if (l >= 0) ++W.start[l + 1];
+    }
+  }
+  for (int64_t r = 0; r < n_rows; ++r) W.start[r + 1] += W.start[r];
+  W.fill.assign(W.start.begin(), W.start.end() - 1);
+  W.pairs.resize(W.start[n_rows]);
+  for (int64_t p = 0; p < ne; ++p)
+    for (int b = 0; b < 4; ++b) {
+      const int32_t l = W.evl[4 * p + b];
+      if (l >= 0) W.pairs[W.fill[l]++] = (int32_t)(4 * p + b);
+    }
+  W.seen.assign(n_rows, -1);
+  if ((int64_t)W.slot_of.size() < n_rows) W.slot_of.resize(n_rows);
+  R.cols.reserve(R.cols.size() + 16 * n_rows);
+  R.ptr.reserve(R.ptr.size() + n_rows);
+  R.inc_tet.reserve(R.inc_tet.size() + W.start[n_rows]);
+  R.inc_code.reserve(R.inc_code.size() + W.start[n_rows]);
+  R.inc_ptr.reserve(R.inc_ptr.size() + n_rows);
+  for (int64_t row = 0; row < n_rows; ++row) {
+    auto& cand = W.cand;
     cand.clear();
-    for (int64_t q = n2t_ptr[g]; q < n2t_ptr[g + 1]; ++q) {
-      int32_t e = n2t[q];
-      if (!tflag[e]) continue;
+    for (int64_t k = W.start[row]; k < W.start[row + 1]; ++k) {
+      const int32_t* ev = W.evl.data() + (W.pairs[k] & ~3);
       for (int b = 0; b < 4; ++b) {
-        int32_t vb = tets[4 * (int64_t)e + b];
-        if (mark[vb] != stamp) continue;
-        int32_t l = loc[vb];
-        if (seen[l] != row) {
-          seen[l] = row;
+        const int32_t l = ev[b];
+        if (l >= 0 && W.seen[l] != row) {
+          W.seen[l] = (int32_t)row;
           cand.push_back(l);
         }
       }
     }
     std::sort(cand.begin(), cand.end());
-    for (size_t k = 0; k < cand.size(); ++k) slot_of[cand[k]] = (int32_t)k;
+    for (size_t k = 0; k < cand.size(); ++k) W.slot_of[cand[k]] = (int32_t)k;
     R.cols.insert(R.cols.end(), cand.begin(), cand.end());
     R.ptr.push_back((int64_t)R.cols.size());
-    for (int64_t q = n2t_ptr[g]; q < n2t_ptr[g + 1]; ++q) {
-      int32_t e = n2t[q];
-      if (!tflag[e]) continue;
-      uint32_t code = 0;
+    for (int64_t k = W.start[row]; k < W.start[row + 1]; ++k) {
+      const int32_t pb = W.pairs[k];
+      const int32_t* ev = W.evl.data() + (pb & ~3);
+      uint32_t code = (uint32_t)(pb & 3);
       for (int b = 0; b < 4; ++b) {
-        int32_t vb = tets[4 * (int64_t)e + b];
-        if (vb == g) code |= (uint32_t)b;
-        uint32_t slot = mark[vb] == stamp ? (uint32_t)slot_of[loc[vb]] : kNoSlot;
+        const uint32_t slot = ev[b] >= 0 ? (uint32_t)W.slot_of[ev[b]] : kNoSlot;
         code |= slot << (2 + 7 * b);
       }
-      R.inc_tet.push_back(e);
+      R.inc_tet.push_back(elems[pb >> 2]);
       R.inc_code.push_back(code);
     }
     R.inc_ptr.push_back((int64_t)R.inc_tet.size());
-    ++row;
   }
 }
 
@@ -154,16 +180,20 @@ void pack_ell(const std::vector<SubOut>& outs, bool plus, const std::vector<int6
   const int n_sd = (int)outs.size();
   std::vector<int32_t> len(n_rows, 0);
   inc_ptr.assign(n_rows + 1, 0);
-  for (int i = 0; i < n_sd; ++i) {
+  std::vector<int32_t> wmax(n_sd, 0);
+  parallel_for(n_sd, n_threads, [&](int i, int) {
     const LocalRows& R = plus ? outs[i].P : outs[i].W;
+    int32_t m = 0;
     for (size_t r = 0; r + 1 < R.ptr.size(); ++r) {
       len[off[i] + r] = (int32_t)(R.ptr[r + 1] - R.ptr[r]);
+      m = std::max(m, len[off[i] + r]);
       inc_ptr[off[i] + r + 1] = R.inc_ptr[r + 1] - R.inc_ptr[r];
     }
-  }
+    wmax[i] = m;
+  });
   for (int64_t r = 0; r < n_rows; ++r) inc_ptr[r + 1] += inc_ptr[r];
   int32_t W = 0;
-  for (int64_t r = 0; r < n_rows; ++r) W = std::max(W, len[r]);
+  for (int i = 0; i < n_sd; ++i) W = std::max(W, wmax[i]);
   const int64_t n_slices = (n_rows + kSlice - 1) / kSlice;
   E.n_rows = n_rows;
   E.W = W;
@@ -283,15 +313,78 @@ int build_global_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
   g.n_sd = n_sd;
   g.r_hops = r_hops;
 
-  // global node -> element incidence (ascending element ids)
+  // global node -> element incidence (ascending element ids): counts and slots taken
+  // with atomics on all cores, then every node's list sorted
+  const int nthr_g = (int)std::min(32u, std::max(1u, std::thread::hardware_concurrency()));
   g.n2t_ptr.assign(n_nodes + 1, 0);
-  for (int64_t q = 0; q < 4 * n_tets; ++q) g.n2t_ptr[tets[q] + 1]++;
-  for (int64_t v = 0; v < n_nodes; ++v) g.n2t_ptr[v + 1] += g.n2t_ptr[v];
-  g.n2t.assign(4 * n_tets, 0);
+  g.n2t.resize(4 * n_tets);
   {
-    std::vector<int64_t> fill(g.n2t_ptr.begin(), g.n2t_ptr.end() - 1);
-    for (int64_t e = 0; e < n_tets; ++e)
-      for (int a = 0; a < 4; ++a) g.n2t[fill[tets[4 * e + a]]++] = (int32_t)e;
+    std::vector<std::atomic<int64_t>> cnt(n_nodes);
+    const int64_t ech = 1 << 16;
+    const int n_ech = (int)((n_tets + ech - 1) / ech);
+    parallel_for((int)((n_nodes + ech - 1) / ech), nthr_g, [&](int c, int) {
+      const int64_t v1 = std::min(n_nodes, (int64_t)(c + 1) * ech);
+      for (int64_t v = (int64_t)c * ech; v < v1; ++v) cnt[v].store(0, std::memory_order_relaxed);
+    });
+    parallel_for(n_ech, nthr_g, [&](int c, int) {
+      const int64_t e1 = std::min(n_tets, (int64_t)(c + 1) * ech);
+      for (int64_t q = 4 * (int64_t)c * ech; q < 4 * e1; ++q)
+        cnt[tets[q]].fetch_add(1, std::memory_order_relaxed);
+    });
+    for (int64_t v = 0; v < n_nodes; ++v)
+      g.n2t_ptr[v + 1] = g.n2t_ptr[v] + cnt[v].load(std::memory_order_relaxed);
+    parallel_for((int)((n_nodes + ech - 1) / ech), nthr_g, [&](int c, int) {
+      const int64_t v1 = std::min(n_nodes, (int64_t)(c + 1) * ech);
+      for (int64_t v = (int64_t)c * ech; v < v1; ++v)
+        cnt[v].store(g.n2t_ptr[v], std::memory_order_relaxed);
+    });
+    parallel_for(n_ech, nthr_g, [&](int c, int) {
+      const int64_t e1 = std::min(n_tets, (int64_t)(c + 1) * ech);
+      for (int64_t e = (int64_t)c * ech; e < e1; ++e)
+        for (int a = 0; a < 4; ++a)
+          g.n2t[cnt[tets[4 * e + a]].fetch_add(1, std::memory_order_relaxed)] = (int32_t)e;
+    });
+    parallel_for((int)((n_nodes + ech - 1) / ech), nthr_g, [&](int c, int) {
+      const int64_t v1 = std::min(n_nodes, (int64_t)(c + 1) * ech);
+      for (int64_t v = (int64_t)c * ech; v < v1; ++v)
+        std::sort(g.n2t.begin() + g.n2t_ptr[v], g.n2t.begin() + g.n2t_ptr[v + 1]);
+    });
+  }
+
+  // node adjacency (nodes sharing an element), for the r-hop balls: two passes over
+  // chunks of nodes, each node deduplicating its element neighbours locally
+  {
+    const int64_t ach = 1 << 13;
+    const int n_ach = (int)((n_nodes + ach - 1) / ach);
+    g.adj_ptr.assign(n_nodes + 1, 0);
+    auto neighbours = [&](int64_t v, std::vector<int32_t>& nb) {
+      nb.clear();
+      for (int64_t q = g.n2t_ptr[v]; q < g.n2t_ptr[v + 1]; ++q)
+        for (int b = 0; b < 4; ++b) {
+          const int32_t w = tets[4 * (int64_t)g.n2t[q] + b];
+          if (w != v) nb.push_back(w);
+        }
+      std::sort(nb.begin(), nb.end());
+      nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+    };
+    parallel_for(n_ach, nthr_g, [&](int c, int) {
+      std::vector<int32_t> nb;
+      const int64_t v1 = std::min(n_nodes, (int64_t)(c + 1) * ach);
+      for (int64_t v = (int64_t)c * ach; v < v1; ++v) {
+        neighbours(v, nb);
+        g.adj_ptr[v + 1] = (int64_t)nb.size();
+      }
+    });
+    for (int64_t v = 0; v < n_nodes; ++v) g.adj_ptr[v + 1] += g.adj_ptr[v];
+    g.adj.resize(g.adj_ptr[n_nodes]);
+    parallel_for(n_ach, nthr_g, [&](int c, int) {
+      std::vector<int32_t> nb;
+      const int64_t v1 = std::min(n_nodes, (int64_t)(c + 1) * ach);
+      for (int64_t v = (int64_t)c * ach; v < v1; ++v) {
+        neighbours(v, nb);
+        std::copy(nb.begin(), nb.end(), g.adj.begin() + g.adj_ptr[v]);
+      }
+    });
   }
 
   // owned nodes per subdomain (ascending)
@@ -336,28 +429,22 @@ int build_global_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     int32_t i, j, u, v;
   };
   // Each free node u lists its free neighbours v with owner(v) > owner(u) once, in
-  // ascending order (a few dozen candidates, deduplicated locally), in chunks of nodes
-  // on all cores; the chunks are concatenated in node order and a stable sort by
-  // subdomain pair then yields the entries ordered by (i, j, u, v).
-  const int64_t chunk = 1 << 16;
+  // ascending order (from the adjacency), in chunks of nodes on all cores; the chunks
+  // are concatenated in node order and a stable sort by subdomain pair then yields the
+  // entries ordered by (i, j, u, v).
+  const int64_t chunk = 1 << 13;
   const int n_chunks = (int)((n_nodes + chunk - 1) / chunk);
   std::vector<std::vector<Entry>> parts(n_chunks);
-  const int nthr_e = (int)std::min(32u, std::max(1u, std::thread::hardware_concurrency()));
-  parallel_for(n_chunks, nthr_e, [&](int c, int) {
-    std::vector<int32_t> nb;
+  parallel_for(n_chunks, nthr_g, [&](int c, int) {
     auto& out = parts[c];
     const int64_t u1 = std::min(n_nodes, (int64_t)(c + 1) * chunk);
     for (int64_t u = (int64_t)c * chunk; u < u1; ++u) {
       if (dirichlet[u]) continue;
-      nb.clear();
-      for (int64_t q = g.n2t_ptr[u]; q < g.n2t_ptr[u + 1]; ++q)
-        for (int b = 0; b < 4; ++b) {
-          int32_t v = tets[4 * (int64_t)g.n2t[q] + b];
-          if (!dirichlet[v] && owner[v] > owner[u]) nb.push_back(v);
-        }
-      std::sort(nb.begin(), nb.end());
-      nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
-      for (int32_t v : nb) out.push_back(Entry{owner[u], owner[v], (int32_t)u, v});
+      for (int64_t q = g.adj_ptr[u]; q < g.adj_ptr[u + 1]; ++q) {
+        const int32_t v = g.adj[q];
+        if (!dirichlet[v] && owner[v] > owner[u])
+          out.push_back(Entry{owner[u], owner[v], (int32_t)u, v});
+      }
     }
   });
   std::vector<Entry> ents;
@@ -436,15 +523,14 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     for (int h = 0; h < g.r_sd[i]; ++h) {
       next.clear();
       for (int32_t v : frontier)
-        for (int64_t q = n2t_ptr[v]; q < n2t_ptr[v + 1]; ++q)
-          for (int b = 0; b < 4; ++b) {
-            int32_t w = tets[4 * (int64_t)n2t[q] + b];
-            if (S.ball[w] != st) {
-              S.ball[w] = st;
-              next.push_back(w);
-              ball_list.push_back(w);
-            }
+        for (int64_t q = g.adj_ptr[v]; q < g.adj_ptr[v + 1]; ++q) {
+          const int32_t w = g.adj[q];
+          if (S.ball[w] != st) {
+            S.ball[w] = st;
+            next.push_back(w);
+            ball_list.push_back(w);
           }
+        }
       frontier.swap(next);
     }
     // T_i^+ = elements touching the ball, ascending
@@ -522,12 +608,10 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
     so.o2w_local.resize(ss.owned.size());
     for (size_t o = 0; o < ss.owned.size(); ++o) so.o2w_local[o] = S.wloc[ss.owned[o]];
     if (so.err.empty()) {
-      std::vector<int32_t> prow(ss.Ip);
-      prow.insert(prow.end(), ss.Bp.begin(), ss.Bp.end());
-      build_rows(prow, tets, n2t_ptr, n2t, S.tplus, S.loc_mark, S.loc, st, so.P, S.seen,
-                 S.slot_of);
-      build_rows(ss.omega, tets, n2t_ptr, n2t, S.tomega, S.wmark, S.wloc, st, so.W, S.seen,
-                 S.slot_of);
+      build_rows((int64_t)(ss.Ip.size() + ss.Bp.size()), ss.plus_tets, tets, S.loc_mark,
+                 S.loc, st, so.P, S.rows);
+      build_rows((int64_t)ss.omega.size(), ss.omega_tets, tets, S.wmark, S.wloc, st, so.W,
+                 S.rows);
     }
     // clear the element flags for the next subdomain on this thread
     for (int32_t e : ss.plus_tets) S.tplus[e] = 0;
@@ -572,7 +656,7 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
   hp.o2w.resize(hp.nO);
   hp.o_node.resize(hp.nO);
   hp.o_sd.resize(hp.nO);
-  for (int i = 0; i < n_sd; ++i) {
+  parallel_for(n_sd, nthr, [&](int i, int) {
     const SubSets& ss = hp.sets[i];
     int64_t p0 = hp.Poff[i], w0 = hp.Woff[i], o0 = hp.Ooff[i];
     for (size_t l = 0; l < ss.Ip.size(); ++l) {
@@ -598,7 +682,7 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
       hp.o_node[o0 + o] = ss.owned[o];
       hp.o_sd[o0 + o] = i;
     }
-  }
+  });
   pack_ell(outs, true, hp.Poff, hp.nP, hp.pat_P, hp.incP_ptr, hp.incP_tet, hp.incP_code,
            nthr);
   pack_ell(outs, false, hp.Woff, hp.nW, hp.pat_W, hp.incW_ptr, hp.incW_tet, hp.incW_code,

@@ -94,6 +94,9 @@ struct HostPlan {
   // global node -> element incidence
   std::vector<int64_t> n2t_ptr;
   std::vector<int32_t> n2t;
+  // global plan only: node adjacency over element edges (ascending, without the node)
+  std::vector<int64_t> adj_ptr;
+  std::vector<int32_t> adj;
 };
 
 // Aggregates of the coarse level of the local preconditioner: the I rows and the B rows
