@@ -171,7 +171,9 @@ typedef struct {
                           spatial aggregates of about coarse_rows rows (runs of the
                           Morton-ordered rows of a subdomain, at most 1024 per
                           subdomain) and E = Z^T A Z inverted per subdomain; 0: Jacobi
-                          only.  Changes iteration counts, not the solutions.         */
+                          only; < 0 (default): 35 in MOR_MIXED, 100 in MOR_FP64 (the
+                          coarse product runs in the working precision).  Changes
+                          iteration counts, not the solutions.                        */
   int32_t h1_weighted; /* 0: the H1 inner product of H_i and H^+ is the unweighted
                           int grad w . grad v + w v of Sec. 4 (as printed); 1: its
                           gradient part is weighted by the coefficient k, a variant for
@@ -205,7 +207,7 @@ typedef struct {
 
 /* Fill opts with defaults (rank 8, oversample 5, seed 0, MOR_MIXED, cg_rtol 1e-9,
  * max_iter 20000, replace_every 40, normwise 1, drift_restart 1.5, sketch_rtol 0,
- * tau 1e-12, orth_tol 1e-14, coarse_rows 35, h1_weighted 0, sketch_div 0, sub_begin 0,
+ * tau 1e-12, orth_tol 1e-14, coarse_rows -1, h1_weighted 0, sketch_div 0, sub_begin 0,
  * sub_end 0, tc_gram 1, explicit_svd 0). */
 int mor_basis_opts_default(mor_basis_opts* opts);
 

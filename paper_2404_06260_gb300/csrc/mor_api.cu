@@ -504,7 +504,7 @@ int mor_basis_opts_default(mor_basis_opts* o) {
   o->sketch_rtol = 0.0;
   o->tau = 1e-12;
   o->orth_tol = 1e-14;
-  o->coarse_rows = 35;
+  o->coarse_rows = -1;
   o->h1_weighted = 0;
   o->sketch_div = 0;
   o->tc_gram = 1;
@@ -911,9 +911,12 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   if (h_err) return fail(MOR_ERR_BAD_MESH, "mor_build_bases: element with non-positive volume");
 
   // ---- coarse level of the local preconditioner (set 0: A_II, set 1: H^+) ----
-  if (o.coarse_rows > 0) {
+  // automatic size: small aggregates where the coarse product runs in binary32 (fewer
+  // iterations for a cheap product), larger ones at GB300's low binary64 rate
+  const int coarse_rows = o.coarse_rows < 0 ? (B.mixed ? 35 : 100) : o.coarse_rows;
+  if (coarse_rows > 0) {
     AggPlan ap;
-    build_aggregates(hp, o.coarse_rows, kMaxAgg, ap);
+    build_aggregates(hp, coarse_rows, kMaxAgg, ap);
     if (ap.max_slots > kMaxSlots)
       return fail(MOR_ERR_ARG, "mor_build_bases: too many aggregates meet one row tile");
     const int64_t n_agg = ap.aoff[n_sd];

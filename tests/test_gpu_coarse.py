@@ -6,7 +6,7 @@ positive definite input that elimination needs no pivoting and is backward stabl
 the computed inverse is within a small multiple of n u kappa(W) of the exact one
 (u = 2^-24; the checks allow 10 n u kappa(W) in the 2-norm, relative).  Sizes cover one
 pivot, a ragged last pivot block (63, 65, 565) and the 1024 cap.  The preconditioner
-changes iteration counts only: finer aggregates (coarse_rows 35, the default, against
+changes iteration counts only: finer aggregates (coarse_rows 35, the mixed default, against
 100) must cut the iterations of the 64^3 build by at least a tenth and leave its singular
 values and reduced energy where the CG tolerance puts them.
 """

@@ -91,7 +91,7 @@ def test_random_partitions_match_the_oracle(mor, seed):
 
 
 def test_finer_aggregates_pass_the_old_cap(mor):
-    # coarse_rows 35 (the default) on the 64^3 workload: the interior subdomains take
+    # coarse_rows 35 (the mixed default) on the 64^3 workload: the interior subdomains take
     # more than 256 aggregates (the A_II and H^+ sets of the coarse level), still within
     # the caps
     mesh, kappa, owner, p = synth.workload("cube64_p4")
