@@ -190,7 +190,10 @@ typedef struct {
                           range (MOR_ERR_ARG otherwise).                                */
   int32_t tc_gram;     /* MOR_MIXED: 1 (default) forms the H_i-Grams and G_B on the
                           tensor cores (tcgen05, exact 7-bit bf16 slices: entry (i, j)
-                          off by at most about 2^-28 rows max|X_i| max|Y_j|); 2 also
+                          off by at most about 2^-28 rows max|X_i| max|Y_j|), and the
+                          coarse-level product E^{-1} r_c of the local solves for up to
+                          128 columns (bf16 high and low parts of both factors, three
+                          products, FP32 accumulators); 2 also
                           forms the interface blocks of Eq. (23) there, whose error is
                           then relative to the largest a_e-weighted entry of a column
                           (at 1e4 coefficient contrast it moves x^T K~ x away from the

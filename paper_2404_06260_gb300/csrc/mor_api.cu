@@ -928,6 +928,11 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
     TRY(M.alloc((unsigned char**)&yc, (size_t)n_agg * kp * tsz_c, true, st));
     int* d_bad;
     TRY(M.alloc(&d_bad, 1, true, st));
+    // the binary32 path forms the coarse product on the tensor cores (tc_gram >= 1)
+    // for up to 128 columns
+    const bool coarse_tc = B.mixed && o.tc_gram != 0 && kp <= 128;
+    int* d_tc_err = nullptr;
+    if (coarse_tc) TRY(M.alloc(&d_tc_err, 1, true, st));
     // E (binary64, assembled) and the inversion workspace, shared by both matrices
     int n_max[2] = {1, 1};
     int64_t ne_max = 1;
@@ -956,7 +961,9 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
         TRY(M.upload(&toff, ap.toff[set], st));
         TRY(M.upload(&eoff, ap.eoff[set], st));
         const int64_t ne = ap.eoff[set][n_sd];
-        const int nrb = (n_max[set] + kCoarseRows - 1) / kCoarseRows;
+        // partial r_c.y_c per row block: blocks of kCoarseRows (SIMT) or kCoarseTcM rows
+        const int nrb = std::max((n_max[set] + kCoarseRows - 1) / kCoarseRows,
+                                 (n_max[set] + kCoarseTcM - 1) / kCoarseTcM);
         void *einv, *cpart;
         double* dpart;
         TRY(M.alloc((unsigned char**)&einv, (size_t)std::max<int64_t>(ne, 1) * tsz_c, true, st));
@@ -989,6 +996,38 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
           fill(B.co32[set], (const float*)einv, (float*)cpart, (float*)yc);
         else
           fill(B.co64[set], (const double*)einv, (double*)cpart, (double*)yc);
+        if (coarse_tc) {
+          // E^{-1} as tensor-core operand blocks: ceil(n / 128) x ceil(n / 32) per
+          // subdomain, 16 KB each
+          std::vector<int64_t> h_off(n_sd + 1, 0);
+          int blocks_max = 0;
+          for (int i = 0; i < n_sd; ++i) {
+            const int nc = ap.nca[set][i];
+            const int nb = ((nc + kCoarseTcM - 1) / kCoarseTcM) * ((nc + 31) / 32);
+            blocks_max = std::max(blocks_max, nb);
+            h_off[i + 1] = h_off[i] + nb;
+          }
+          int64_t* etc_off;
+          uint4* etc;
+          TRY(M.upload(&etc_off, h_off, st));
+          TRY(M.alloc(&etc, (size_t)std::max<int64_t>(h_off[n_sd], 1) * 1024, false, st));
+          launch_coarse_tc_pack(n_sd, blocks_max, nca, eoff, (const float*)einv, etc_off, etc,
+                                st);
+          // r_c planes: ceil(n / 32) blocks of 2 x NP x 32 bf16 per subdomain
+          const int NP = (kp + 15) & ~15;
+          std::vector<int64_t> h_rc(n_sd + 1, 0);
+          for (int i = 0; i < n_sd; ++i) h_rc[i + 1] = h_rc[i] + (ap.nca[set][i] + 31) / 32;
+          int64_t* rcb_off;
+          __nv_bfloat16* rcb;
+          TRY(M.upload(&rcb_off, h_rc, st));
+          TRY(M.alloc(&rcb, (size_t)std::max<int64_t>(h_rc[n_sd], 1) * 2 * NP * 32, true, st));
+          B.co32[set].rcb = rcb;
+          B.co32[set].rcb_off = rcb_off;
+          B.co32[set].etc = etc;
+          B.co32[set].etc_off = etc_off;
+          B.co32[set].tc_err = d_tc_err;
+          B.co32[set].tc_budget = wait_budget_cycles();
+        }
       }
       CK(cudaStreamSynchronize(st));
     }
@@ -1412,6 +1451,14 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
                        cudaMemcpyDeviceToDevice, st));
     Bo.rbb_off = DW.h_bboff;
     Bo.rbb_m = DW.h_M;
+  }
+  if (B.co32[0].tc_err) {
+    int h_err = 0;
+    CK(cudaMemcpyAsync(&h_err, B.co32[0].tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_err)
+      return fail(MOR_ERR_TIMEOUT, "mor_build_bases: a wait of the tensor-core coarse product "
+                                   "ran out of its budget (mor_set_wait_budget)");
   }
   if (use_tc) {
     int h_tcerr = 0;

@@ -5,6 +5,9 @@
 // not what they compute.
 #include "mor_kernels.h"
 #include "mor_plan.h"
+#include "mor_tc.cuh"
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
@@ -251,7 +254,42 @@ __global__ void k_gj_out(const int32_t* __restrict__ nca, const int64_t* __restr
     }
 }
 
+// the tensor-core operand blocks of E^{-1} (see launch_coarse_tc_pack): one block of
+// 256 threads per (subdomain, 128 x 32 block)
+__global__ void k_coarse_tc_pack(const int32_t* __restrict__ nca,
+                                 const int64_t* __restrict__ eoff,
+                                 const float* __restrict__ einv,
+                                 const int64_t* __restrict__ etc_off, uint4* out) {
+  const int sd = blockIdx.y, n = nca[sd];
+  const int nkb = (n + tc::kKB - 1) / tc::kKB;
+  const int mt = (n + kCoarseTcM - 1) / kCoarseTcM;
+  const int blk = blockIdx.x;
+  if (n <= 0 || blk >= mt * nkb) return;
+  const int m = blk / nkb, kb = blk - m * nkb;
+  const float* E = einv + eoff[sd];
+  // 16 KB per block: two planes of 128 x 32 bf16
+  __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(out + (etc_off[sd] + blk) * 1024);
+  __nv_bfloat16* lo = hi + kCoarseTcM * tc::kKB;
+  for (int idx = threadIdx.x; idx < kCoarseTcM * tc::kKB; idx += blockDim.x) {
+    const int r = idx / tc::kKB, k = idx - r * tc::kKB;
+    const int a = m * kCoarseTcM + r, b = kb * tc::kKB + k;
+    const float v = (a < n && b < n) ? E[(int64_t)a * n + b] : 0.0f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const uint32_t o = tc::kmajor(r, k) >> 1;
+    hi[o] = h;
+    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 }  // namespace
+
+void launch_coarse_tc_pack(int n_sd, int blocks_max, const int32_t* nca, const int64_t* eoff,
+                           const float* einv, const int64_t* etc_off, uint4* out,
+                           cudaStream_t st) {
+  if (n_sd <= 0 || blocks_max <= 0) return;
+  count_launch();
+  k_coarse_tc_pack<<<dim3(blocks_max, n_sd), 256, 0, st>>>(nca, eoff, einv, etc_off, out);
+}
 
 void launch_coarse_matrix(const DTiles& tiles, const EllView<double>& A, const int32_t* aloc,
                           const int32_t* nca, const int64_t* eoff, double* E, cudaStream_t st) {

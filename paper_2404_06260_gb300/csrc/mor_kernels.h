@@ -8,6 +8,8 @@
 
 #include "mor_dev.cuh"
 
+#include <cuda_bf16.h>
+
 namespace mor {
 
 // host-side count of kernel launches issued by the library (every launcher adds its
@@ -117,6 +119,17 @@ struct Coarse {
   T* yc = nullptr;                  // global aggregates x kp: E^{-1} Z^T r
   double* dpart = nullptr;          // n_sd x row blocks x kp: partial r_c . y_c
   int n_max = 0;                    // largest nca
+  // binary32 path with the tensor-core product (null: binary32 / binary64 SIMT):
+  // E^{-1} as bf16 hi / lo planes in tcgen05 operand blocks (launch_coarse_tc_pack),
+  // the first block of each subdomain, and the flag a timed-out wait sets
+  const uint4* etc = nullptr;
+  const int64_t* etc_off = nullptr;
+  // r_c of every step as bf16 high and low planes, 2 x NP x 32 per 32-aggregate block
+  // (NP = kp rounded up to 16), the first block of each subdomain at rcb_off[sd]
+  __nv_bfloat16* rcb = nullptr;
+  const int64_t* rcb_off = nullptr;
+  int* tc_err = nullptr;
+  long long tc_budget = 0;
 };
 
 template <typename T>
@@ -205,6 +218,14 @@ void launch_coarse_invert(int n_sd, int n_max, const int32_t* nca, const int64_t
                           const double* E, float* W, float* P, double* sc, T* einv, int* bad,
                           cudaStream_t st);
 constexpr int kCoarsePivots = 64;  // pivot block of launch_coarse_invert
+// E^{-1} of every subdomain as tcgen05 A-operand blocks for y_c = E^{-1} r_c: block
+// (m * nkb + kb) of subdomain sd (at etc_off[sd], 16 KB each, nkb = ceil(n / 32)) holds
+// E^{-1}[128 m + r][32 kb + k] (zero outside n) split into a bf16 high part and the
+// bf16 rounding of the remainder, two K-major planes of 128 x 32.
+constexpr int kCoarseTcM = 128;  // rows of y_c per tensor-core block (the MMA M)
+void launch_coarse_tc_pack(int n_sd, int blocks_max, const int32_t* nca, const int64_t* eoff,
+                           const float* einv, const int64_t* etc_off, uint4* out,
+                           cudaStream_t st);
 // x64 += xT, xT = 0
 template <typename T>
 void launch_accum_reset(const DTiles& tiles, T* xT, double* x64, int kp, cudaStream_t st);

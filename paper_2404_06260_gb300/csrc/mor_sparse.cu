@@ -8,6 +8,9 @@
 // last tile of a subdomain to finish (atomic ticket) reduces them in tile order, so the
 // reductions are deterministic and need no extra launch.
 #include "mor_kernels.h"
+#include "mor_tc.cuh"
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <mutex>
@@ -663,6 +666,83 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4)
   }
 }
 
+constexpr int kCoarseCols = 16;
+enum { kCoarseInit = 0, kCoarseStep = 1, kCoarseReplace = 2 };
+
+// The last block of a subdomain in the coarse kernels: r.M^{-1}r = fine part + the
+// nrb row blocks' parts of r_c.y_c (in order); mode STEP: the convergence test on the
+// recursive residual, beta and gam, the work counts (cw: columns per chunk, each open
+// chunk reads E^{-1} once) and the active count; INIT / REPLACE: rz only.
+template <typename T>
+__device__ void coarse_finish(const Geo& g, const DTiles& tl, int sd, int kp, int cw, int nrb,
+                              double tol2, int mode, CgState& s, const Coarse<T>& co) {
+  constexpr int PN = Pack<T>::N;
+  const int nchunk = (kp + cw - 1) / cw;
+  // the subdomain's columns: open packs before the update (the sparse product and the
+  // x/r update of this step worked on them), the test and beta, open packs after
+  __shared__ int open_pre, open_post, chunks_open;
+  const bool count = s.work && mode == kCoarseStep;
+  if (g.tid == 0) open_pre = open_post = chunks_open = 0;
+  __syncthreads();
+  if (count) {
+    for (int pk = g.tid; pk * PN < kp; pk += g.nth) {
+      bool open = false;
+      for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + pk * PN + e];
+      if (open) atomicAdd(&open_pre, 1);
+    }
+    for (int ch = g.tid; ch < nchunk; ch += g.nth) {
+      bool open = false;
+      for (int j = 0; j < cw && ch * cw + j < kp; ++j) open = open || !s.done[sd * kp + ch * cw + j];
+      if (open) atomicAdd(&chunks_open, 1);
+    }
+  }
+  __syncthreads();
+  for (int c = g.tid; c < kp; c += g.nth) {
+    const int i = sd * kp + c;
+    double cd = 0.0;
+    if (co.dpart)
+      for (int r = 0; r < nrb; ++r) cd += __ldcg(co.dpart + ((int64_t)sd * nrb + r) * kp + c);
+    const double rzn = s.rzf[i] + cd;
+    if (mode == kCoarseStep) {
+      double be = 0.0;
+      if (!s.done[i]) {
+        if (s.rr[i] <= tol2 * s.bb[i] || !(s.rz[i] > 0.0)) {
+          s.done[i] = 1;
+        } else {
+          be = rzn / s.rz[i];
+          s.rz[i] = rzn;
+        }
+      }
+      set_coef(s.beta, s.beta32, i, be);
+      set_coef(s.gam, s.gam32, i, 1.0);
+    } else {
+      s.rz[i] = rzn;
+    }
+  }
+  if (mode != kCoarseStep) return;
+  __syncthreads();
+  if (count) {
+    for (int pk = g.tid; pk * PN < kp; pk += g.nth) {
+      bool open = false;
+      for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + pk * PN + e];
+      if (open) atomicAdd(&open_post, 1);
+    }
+    __syncthreads();
+    if (g.tid == 0) {
+      // work counts of the algorithmic-bytes model
+      const int nsd = tl.n_sd;
+      const unsigned long long rows = (unsigned long long)s.sd_rows[sd];
+      const unsigned long long nc = co.aloc ? (unsigned long long)co.nca[sd] : 0ull;
+      atomicAdd(s.work + sd, (unsigned long long)s.sd_nnz[sd]);
+      atomicAdd(s.work + nsd + sd, (unsigned long long)open_pre * rows);
+      atomicAdd(s.work + 2 * nsd + sd, (unsigned long long)open_post * rows);
+      if (nc) atomicAdd(s.work + 3 * nsd + sd, (unsigned long long)chunks_open * nc * nc);
+    }
+  }
+  count_active(g, s.done, sd, kp, s.active);
+  if (g.tid == 0 && s.active[sd] > 0) s.iters[sd] += 1;
+}
+
 // Coarse level of one subdomain (grid: x = row block x column chunk, y = subdomain).
 // Block (rb, chunk) forms r_c = Z^T r for the chunk's kCoarseCols columns from the tile
 // partials, then rows [rb kCoarseRows, (rb + 1) kCoarseRows) of y_c = E^{-1} r_c (stored
@@ -672,11 +752,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 4)
 // beta = (r.z)_new / (r.z)_old; INIT / REPLACE: rz only (beta and gam come from the init
 // / replacement kernel).  Without a coarse level y_c = 0.  The blocks of one row block
 // are adjacent in the grid, so the chunks read its E^{-1} rows from L2 after the first.
-constexpr int kCoarseCols = 16;
 constexpr int kCoarseRpt = 2;  // rows of y_c per thread
 constexpr int kCoarseThreads = kCoarseRows / kCoarseRpt;
 constexpr size_t kCoarseRedBytes = sizeof(double) * (kCoarseThreads / 32) * kCoarseCols;
-enum { kCoarseInit = 0, kCoarseStep = 1, kCoarseReplace = 2 };
 template <typename T>
 __global__ void __launch_bounds__(kCoarseThreads)
     k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s, Coarse<T> co) {
@@ -797,69 +875,272 @@ __global__ void __launch_bounds__(kCoarseThreads)
     }
   }
   if (!last_block(g, s.counter, sd, gridDim.x)) return;
-  // the subdomain's columns: open packs before the update (the sparse product and the
-  // x/r update of this step worked on them), the test and beta, open packs after
-  __shared__ int open_pre, open_post, chunks_open;
-  const bool count = s.work && mode == kCoarseStep;
-  if (g.tid == 0) open_pre = open_post = chunks_open = 0;
-  __syncthreads();
-  if (count) {
-    for (int pk = g.tid; pk * PN < kp; pk += g.nth) {
-      bool open = false;
-      for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + pk * PN + e];
-      if (open) atomicAdd(&open_pre, 1);
-    }
-    for (int ch = g.tid; ch < nchunk; ch += g.nth) {
-      bool open = false;
-      for (int j = 0; j < cw && ch * cw + j < kp; ++j) open = open || !s.done[sd * kp + ch * cw + j];
-      if (open) atomicAdd(&chunks_open, 1);
+  coarse_finish<T>(g, tl, sd, kp, cw, nrb, tol2, mode, s, co);
+}
+
+// The coarse product of the binary32 path on the tensor cores, y_c = E^{-1} r_c for
+// every column (NP = kp rounded up to 16, at most 128), in two kernels.
+// k_coarse_rc_pack forms r_c = Z^T r per 32-aggregate block from the tile partials and
+// stores it as bf16 high and low planes in the K-major operand layout (row = column of
+// r_c).  k_cg_coarse_tc then runs block (m, sd): rows [128 m, 128 m + 128) of y_c as
+// one tcgen05 MMA tile with its FP32 accumulator in TMEM, A = E^{-1} (launch_coarse_tc_
+// pack) and B = r_c streamed through kTcStages shared-memory stages by cp.async, and
+// three products hi.hi + hi.lo + lo.hi per block (about 16 significant bits of each
+// factor; the dropped lo.lo term is below 2^-16 of a product, under the binary32
+// accumulation error of a 1,000-term sum).  One thread issues the MMAs and commits them
+// to the stage's mbarrier; a stage is refilled once its MMAs are done, and every wait
+// is bounded (a timeout sets co.tc_err and ends the block after its MMAs drain).  The
+// epilogue reads the accumulator rows (tcgen05.ld, one row per thread), stores y_c and
+// this block's part of r_c.y_c; the last block of the subdomain finishes as in
+// k_cg_coarse.
+constexpr int kTcThreads = 128;  // one thread per accumulator row (TMEM lane)
+constexpr int kTcStages = 4;
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+// r_c pack (aggregate a of subdomain sd, columns 4 pk .. 4 pk + 3), zero outside n, kp
+__device__ __forceinline__ Pack<float> restrict_pack(const DTiles& tl, const Coarse<float>& co,
+                                                     int a0, int n, int kp, int a, int pk) {
+  Pack<float> v;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) v.v[e] = 0.0f;
+  if (a < n && 4 * pk < kp) {
+    const int ga = a0 + a;
+    const int t0 = co.tfirst[ga], tn = co.tcount[ga];
+    for (int t = t0; t < t0 + tn; ++t) {
+      const int slot = a - co.aloc[tl.r0[t]];
+      const Pack<float> pv = ld(co.cpart + (co.toff[t] + slot) * kp + 4 * pk);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v.v[e] += pv.v[e];
     }
   }
-  __syncthreads();
-  for (int c = g.tid; c < kp; c += g.nth) {
-    const int i = sd * kp + c;
-    double cd = 0.0;
-    if (co.dpart)
-      for (int r = 0; r < nrb; ++r) cd += __ldcg(co.dpart + ((int64_t)sd * nrb + r) * kp + c);
-    const double rzn = s.rzf[i] + cd;
-    if (mode == kCoarseStep) {
-      double be = 0.0;
-      if (!s.done[i]) {
-        if (s.rr[i] <= tol2 * s.bb[i] || !(s.rz[i] > 0.0)) {
-          s.done[i] = 1;
+  return v;
+}
+// an open column of subdomain sd (the coarse product is skipped without one)
+__device__ __forceinline__ bool any_open_column(const CgState& s, int sd, int kp) {
+  bool open = false;
+  for (int c = 0; c < kp; ++c) open = open || !s.done[sd * kp + c];
+  return open;
+}
+
+// block (kb, sd): r_c of aggregates 32 kb .. 32 kb + 31 into co.rcb at co.rcb_off[sd] + kb
+__global__ void __launch_bounds__(kTcThreads)
+    k_coarse_rc_pack(DTiles tl, int kp, int NP, CgState s, Coarse<float> co) {
+  const int sd = blockIdx.y, kb = blockIdx.x;
+  if (s.active[sd] == 0 || !any_open_column(s, sd, kp)) return;
+  const int n = co.nca[sd];
+  if (kb * tc::kKB >= n) return;
+  const int a0 = co.aoff[sd];
+  __nv_bfloat16* bh = co.rcb + (co.rcb_off[sd] + kb) * (int64_t)(2 * NP * tc::kKB);
+  __nv_bfloat16* bl = bh + NP * tc::kKB;
+  const int npk = NP / 4;
+  for (int idx = threadIdx.x; idx < tc::kKB * npk; idx += blockDim.x) {
+    const int k = idx / npk, pk = idx - k * npk;
+    const Pack<float> v = restrict_pack(tl, co, a0, n, kp, kb * tc::kKB + k, pk);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __nv_bfloat16 h, l;
+      split_bf16(v.v[e], h, l);
+      const uint32_t o = tc::kmajor(4 * pk + e, k) >> 1;
+      bh[o] = h;
+      bl[o] = l;
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads)
+    k_cg_coarse_tc(DTiles tl, int kp, int NP, double tol2, int mode, CgState s,
+                   Coarse<float> co) {
+  constexpr int KB = tc::kKB;
+  constexpr int A_PLANE = kCoarseTcM * KB * 2;  // bytes
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int B_PLANE = NP * KB * 2;
+  const int STAGE = 2 * A_PLANE + 2 * B_PLANE;  // A hi, A lo, B hi, B lo
+  double* red = reinterpret_cast<double*>(smem + kTcStages * STAGE);  // 4 warps x NP
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar[kTcStages];
+  __shared__ int s_ok;
+  Geo g = geo();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sd = blockIdx.y, mt = blockIdx.x, nmt = gridDim.x;
+  if (s.active[sd] == 0) return;
+  const int n = (co.aloc && any_open_column(s, sd, kp)) ? co.nca[sd] : 0;
+  const int a_lo = mt * kCoarseTcM;
+  for (int c = tid; c < 4 * NP; c += kTcThreads) red[c] = 0.0;
+  if (a_lo < n) {
+    const int a0 = co.aoff[sd];
+    const int nkb = (n + KB - 1) / KB;
+    const unsigned char* Ag =
+        reinterpret_cast<const unsigned char*>(co.etc + (co.etc_off[sd] + (int64_t)mt * nkb) * 1024);
+    const unsigned char* Bg =
+        reinterpret_cast<const unsigned char*>(co.rcb + co.rcb_off[sd] * (int64_t)(2 * NP * KB));
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(smem);
+    // block kb's operands into stage stg: 16-byte asynchronous copies, one group
+    auto issue = [&](int kb, int stg) {
+      if (kb < nkb) {
+        const uint32_t sa = s0 + (uint32_t)(stg * STAGE);
+        const unsigned char* ga = Ag + (int64_t)kb * (2 * A_PLANE);
+        for (int i = tid; i < 2 * A_PLANE / 16; i += kTcThreads)
+          cp_async16(sa + 16 * i, ga + 16 * i);
+        const unsigned char* gb = Bg + (int64_t)kb * (2 * B_PLANE);
+        for (int i = tid; i < 2 * B_PLANE / 16; i += kTcThreads)
+          cp_async16(sa + 2 * A_PLANE + 16 * i, gb + 16 * i);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)NP) ncols <<= 1;
+    if (warp == 0) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                   ::"r"(dst), "r"(ncols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+      for (int q = 0; q < kTcStages; ++q) {
+        const uint32_t mq = (uint32_t)__cvta_generic_to_shared(&mbar[q]);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mq), "r"(1));
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;");
+      s_ok = 1;
+    }
+    for (int q = 0; q < kTcStages - 1; ++q) issue(q, q);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = tmem_base;
+    const uint32_t idesc = tc::instr_desc(kCoarseTcM, NP);
+    uint32_t ph = 0;  // bit q: parity of the next completion of stage q's mbarrier
+    bool ok = true;
+    int last = -1;  // stage of the last committed MMAs
+    for (int kb = 0; kb < nkb && ok; ++kb) {
+      const int stg = kb % kTcStages;
+      // block kb's copies are done (at most kTcStages - 2 newer groups pending)
+      asm volatile("cp.async.wait_group %0;" ::"n"(kTcStages - 2) : "memory");
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+        const uint32_t sa = s0 + (uint32_t)(stg * STAGE);
+        const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};  // hi.hi, hi.lo, lo.hi
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+          for (int ks = 0; ks < KB / 16; ++ks) {
+            const uint64_t ad =
+                tc::smem_desc(sa + (uint32_t)(pa[q] * A_PLANE + ks * 256), 128, (KB / 8) * 128);
+            const uint64_t bd = tc::smem_desc(
+                sa + (uint32_t)(2 * A_PLANE + pb[q] * B_PLANE + ks * 256), 128, (KB / 8) * 128);
+            const uint32_t en = (kb == 0 && q == 0 && ks == 0) ? 0u : 1u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tbase),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(en));
+          }
+        const uint32_t mq = (uint32_t)__cvta_generic_to_shared(&mbar[stg]);
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                mq));
+      }
+      __syncwarp();
+      last = stg;
+      // refill the stage of block kb - 1 (block kb + kTcStages - 1) once its MMAs are done
+      if (kb >= 1) {
+        const int ps = (kb - 1) % kTcStages;
+        const uint32_t mq = (uint32_t)__cvta_generic_to_shared(&mbar[ps]);
+        if (tc::mbar_wait(mq, (ph >> ps) & 1u, co.tc_budget)) {
+          ph ^= 1u << ps;
         } else {
-          be = rzn / s.rz[i];
-          s.rz[i] = rzn;
+          atomicExch(co.tc_err, 1);
+          s_ok = 0;
         }
       }
-      set_coef(s.beta, s.beta32, i, be);
-      set_coef(s.gam, s.gam32, i, 1.0);
-    } else {
-      s.rz[i] = rzn;
+      issue(kb + kTcStages - 1, (kb + kTcStages - 1) % kTcStages);
+      __syncthreads();
+      ok = s_ok != 0;
     }
-  }
-  if (mode != kCoarseStep) return;
-  __syncthreads();
-  if (count) {
-    for (int pk = g.tid; pk * PN < kp; pk += g.nth) {
-      bool open = false;
-      for (int e = 0; e < PN; ++e) open = open || !s.done[sd * kp + pk * PN + e];
-      if (open) atomicAdd(&open_post, 1);
+    // the last block's MMAs (the others were waited for before their refills)
+    if (ok && last >= 0) {
+      const uint32_t mq = (uint32_t)__cvta_generic_to_shared(&mbar[last]);
+      if (tc::mbar_wait(mq, (ph >> last) & 1u, co.tc_budget)) {
+        ph ^= 1u << last;
+      } else {
+        atomicExch(co.tc_err, 1);
+        s_ok = 0;
+      }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (g.tid == 0) {
-      // work counts of the algorithmic-bytes model
-      const int nsd = tl.n_sd;
-      const unsigned long long rows = (unsigned long long)s.sd_rows[sd];
-      const unsigned long long nc = co.aloc ? (unsigned long long)co.nca[sd] : 0ull;
-      atomicAdd(s.work + sd, (unsigned long long)s.sd_nnz[sd]);
-      atomicAdd(s.work + nsd + sd, (unsigned long long)open_pre * rows);
-      atomicAdd(s.work + 2 * nsd + sd, (unsigned long long)open_post * rows);
-      if (nc) atomicAdd(s.work + 3 * nsd + sd, (unsigned long long)chunks_open * nc * nc);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ok = s_ok != 0;
+    if (ok) {
+      // epilogue: row a of the tile is TMEM lane a = thread tid; eight columns per load
+      const int a = a_lo + tid;
+      for (int c0 = 0; c0 < NP; c0 += 8) {
+        uint32_t r[8];
+        const uint32_t ta = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        double dl[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dl[e] = 0.0;
+        if (a < n) {
+          float* yo = co.yc + (int64_t)(a0 + a) * kp;
+#pragma unroll
+          for (int h = 0; h < 8; h += 4) {
+            const Pack<float> rp = restrict_pack(tl, co, a0, n, kp, a, (c0 + h) / 4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int c = c0 + h + e;
+              const float y = __uint_as_float(r[h + e]);
+              if (c < kp) yo[c] = y;
+              dl[h + e] = (double)y * (double)rp.v[e];
+            }
+          }
+        }
+        // rows summed within the warp (fixed shuffle tree), one partial per warp
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          double v = dl[e];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          if (lane == 0) red[warp * NP + c0 + e] = v;
+        }
+      }
+    } else if (last >= 0) {
+      // a wait ran out: wait once more (bounded) for the stages' pending MMAs, so that
+      // they drain before the TMEM is released
+      for (int q = 0; q < kTcStages; ++q) {
+        const uint32_t mq = (uint32_t)__cvta_generic_to_shared(&mbar[q]);
+        tc::mbar_wait(mq, (ph >> q) & 1u, co.tc_budget);
+      }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                   "r"(ncols));
   }
-  count_active(g, s.done, sd, kp, s.active);
-  if (g.tid == 0 && s.active[sd] > 0) s.iters[sd] += 1;
+  __syncthreads();
+  // this block's part of r_c.y_c per column, warps in order
+  for (int c = tid; c < kp; c += kTcThreads) {
+    double t = 0.0;
+    for (int w = 0; w < kTcThreads / 32; ++w) t += red[w * NP + c];
+    co.dpart[((int64_t)sd * nmt + mt) * kp + c] = t;
+  }
+  if (!last_block(g, s.counter, sd, nmt)) return;
+  coarse_finish<float>(g, tl, sd, kp, kp, nmt, tol2, mode, s, co);
 }
 
 // p = gam (D^{-1} r + Z y_c) + beta p (p is not read where beta = 0), and p.r of the
@@ -1095,12 +1376,37 @@ void launch_coarse_then_p(const DTiles& tiles, int n_sd, const T* r, T* p, const
     attr = true;
   }
   const int n_max = co.aloc ? co.n_max : 0;
+  dim3 bl = block_of<T>(kp);
+  count_launch(2);
+  if constexpr (sizeof(T) == 4) {
+    if (co.etc) {
+      // tensor-core product: one block per 128 rows of y_c and subdomain, every column
+      const int NP = (kp + 15) & ~15;
+      const size_t smt = (size_t)kTcStages * (2 * (kCoarseTcM * tc::kKB * 2) +
+                                              2 * NP * tc::kKB * 2) +
+                         sizeof(double) * 4 * NP;
+      static bool attr_tc = false;
+      if (!attr_tc) {
+        cudaFuncSetAttribute((const void*)k_cg_coarse_tc,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_tc = true;
+      }
+      const int nmt = std::max(1, (n_max + kCoarseTcM - 1) / kCoarseTcM);
+      const int nkb = std::max(1, (n_max + tc::kKB - 1) / tc::kKB);
+      count_launch();
+      k_coarse_rc_pack<<<dim3(nkb, n_sd), kTcThreads, 0, st>>>(tiles, kp, NP, s, co);
+      k_cg_coarse_tc<<<dim3(nmt, n_sd), kTcThreads, smt, st>>>(tiles, kp, NP, tol2, mode, s,
+                                                                co);
+      if (ev_mid) cudaEventRecord(*ev_mid, st);
+      k_cg_update_p<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, r, p,
+                                                                             dinv, kp, s, co);
+      return;
+    }
+  }
   const size_t sm = align16(sizeof(T) * ((n_max + 7) & ~7) * kCoarseCols) + kCoarseRedBytes;
   const int nrb = std::max(1, (n_max + kCoarseRows - 1) / kCoarseRows);
   const int nchunk = (kp + kCoarseCols - 1) / kCoarseCols;
   dim3 grid(nrb * nchunk, n_sd);
-  dim3 bl = block_of<T>(kp);
-  count_launch(2);
   k_cg_coarse<T><<<grid, kCoarseThreads, sm, st>>>(tiles, kp, tol2, mode, s, co);
   if (ev_mid) cudaEventRecord(*ev_mid, st);
   k_cg_update_p<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, r, p, dinv,

@@ -27,47 +27,20 @@
 #include <algorithm>
 
 #include "mor_kernels.h"
+#include "mor_tc.cuh"
 
 namespace mor {
 namespace {
 
-constexpr int kKB = 32;        // rows per MMA block (two K = 16 steps)
+constexpr int kKB = tc::kKB;   // rows per MMA block (two K = 16 steps)
 constexpr int kNS = 4;         // slices per value
 constexpr int kM = 128;        // MMA M
 constexpr int kFlush = 8;      // blocks between accumulator flushes (256 rows)
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
-  return d;
-}
-__device__ __forceinline__ uint32_t instr_desc(int M, int N) {
-  return (1u << 4)                       // accumulator FP32
-         | (1u << 7) | (1u << 10)        // A, B bf16
-         | ((uint32_t)(N >> 3) << 17)    // N / 8 (A, B K-major: bits 15, 16 zero)
-         | ((uint32_t)(M >> 4) << 24);   // M / 16
-}
-__device__ __forceinline__ uint32_t kmajor(int r, int k) {
-  return (uint32_t)((r >> 3) * ((kKB / 8) * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, long long budget) {
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(mb), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > budget) return false;
-  }
-}
+using tc::instr_desc;
+using tc::kmajor;
+using tc::mbar_wait;
+using tc::smem_desc;
 
 // the four slices of x * 2^(7 - e) into column c, row k of the four slice planes.  The
 // slicing is integer work on the bits of x (GB300's binary64 rate is low): with

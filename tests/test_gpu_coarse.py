@@ -77,3 +77,25 @@ def test_finer_aggregates_cut_iterations_not_results(mor):
     s100, s35 = out[100][1], out[35][1]
     assert np.max(np.abs(s35 - s100)) <= 1e-7 * s100.max()
     assert abs(out[35][2] - out[100][2]) <= 1e-8 * out[100][2]
+
+
+def test_tensor_core_coarse_product_matches_simt(mor):
+    # tc_gram 1 forms y_c = E^{-1} r_c on the tensor cores (bf16 high and low parts,
+    # three products), tc_gram 0 in binary32 SIMT: the preconditioners differ at the
+    # 1e-5 level, which may move an iteration count by one check interval (8) but not
+    # the bases beyond the CG tolerance
+    mesh, kappa, owner, p = synth.workload("cube64_p4")
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, p["r_hops"])
+    out = {}
+    for tc in (0, 1):
+        b = mor.Bases(sd, mor.basis_opts(rank=p["rank"], oversample=p["oversample"],
+                                         seed=p["seed"], precision="mixed", cg_rtol=1e-9,
+                                         tc_gram=tc))
+        assert b.converged
+        x, info = mor.Reduced(sd, b).solve(rtol=1e-12)
+        out[tc] = (b.stats(), b.sigma(), info["energy"])
+    it0, it1 = out[0][0][:4], out[1][0][:4]
+    assert np.all(np.abs(it1 - it0) <= 8), (it0, it1)
+    assert np.max(np.abs(out[1][1] - out[0][1])) <= 1e-7 * out[0][1].max()
+    assert abs(out[1][2] - out[0][2]) <= 1e-8 * out[0][2]
