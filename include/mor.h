@@ -171,7 +171,7 @@ typedef struct {
                           spatial aggregates of about coarse_rows rows (runs of the
                           Morton-ordered rows of a subdomain, at most 1024 per
                           subdomain) and E = Z^T A Z inverted per subdomain; 0: Jacobi
-                          only; < 0 (default): 35 in MOR_MIXED, 100 in MOR_FP64 (the
+                          only; < 0 (default): 35 in MOR_MIXED, 300 in MOR_FP64 (the
                           coarse product runs in the working precision).  Changes
                           iteration counts, not the solutions.                        */
   int32_t h1_weighted; /* 0: the H1 inner product of H_i and H^+ is the unweighted

@@ -913,7 +913,7 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
   // ---- coarse level of the local preconditioner (set 0: A_II, set 1: H^+) ----
   // automatic size: small aggregates where the coarse product runs in binary32 (fewer
   // iterations for a cheap product), larger ones at GB300's low binary64 rate
-  const int coarse_rows = o.coarse_rows < 0 ? (B.mixed ? 35 : 100) : o.coarse_rows;
+  const int coarse_rows = o.coarse_rows < 0 ? (B.mixed ? 35 : 300) : o.coarse_rows;
   if (coarse_rows > 0) {
     AggPlan ap;
     build_aggregates(hp, coarse_rows, kMaxAgg, ap);
@@ -961,8 +961,9 @@ static int build_bases_core(const mor_subdomains* sd, const mor_basis_opts* opts
         TRY(M.upload(&toff, ap.toff[set], st));
         TRY(M.upload(&eoff, ap.eoff[set], st));
         const int64_t ne = ap.eoff[set][n_sd];
-        // partial r_c.y_c per row block: blocks of kCoarseRows (SIMT) or kCoarseTcM rows
-        const int nrb = std::max((n_max[set] + kCoarseRows - 1) / kCoarseRows,
+        // partial r_c.y_c per row block: blocks of at least kCoarseRowsMin (SIMT) or
+        // kCoarseTcM rows
+        const int nrb = std::max((n_max[set] + kCoarseRowsMin - 1) / kCoarseRowsMin,
                                  (n_max[set] + kCoarseTcM - 1) / kCoarseTcM);
         void *einv, *cpart;
         double* dpart;

@@ -104,7 +104,7 @@ struct CgState {
 // preconditioner is D^{-1} alone.
 constexpr int kMaxSlots = 32;  // aggregates meeting one row tile (host-enforced)
 constexpr int kMaxAgg = 1024;  // aggregates per subdomain and matrix (host-enforced)
-constexpr int kCoarseRows = 512;  // rows of E^{-1} per block of the coarse product
+constexpr int kCoarseRowsMin = 256;  // fewest rows of E^{-1} per block of the SIMT coarse product
 template <typename T>
 struct Coarse {
   const int32_t* aloc = nullptr;    // per P row: aggregate index within its subdomain

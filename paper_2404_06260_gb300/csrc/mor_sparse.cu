@@ -743,21 +743,23 @@ __device__ void coarse_finish(const Geo& g, const DTiles& tl, int sd, int kp, in
   if (g.tid == 0 && s.active[sd] > 0) s.iters[sd] += 1;
 }
 
-// Coarse level of one subdomain (grid: x = row block x column chunk, y = subdomain).
-// Block (rb, chunk) forms r_c = Z^T r for the chunk's kCoarseCols columns from the tile
-// partials, then rows [rb kCoarseRows, (rb + 1) kCoarseRows) of y_c = E^{-1} r_c (stored
-// for the p update), kCoarseRpt rows per thread, and their part of r_c.y_c.  The last block of
-// the subdomain (atomic ticket) adds the parts in row-block order, r.M^{-1}r = fine part
-// + r_c.y_c, and in mode STEP takes the convergence test on the recursive residual and
-// beta = (r.z)_new / (r.z)_old; INIT / REPLACE: rz only (beta and gam come from the init
-// / replacement kernel).  Without a coarse level y_c = 0.  The blocks of one row block
-// are adjacent in the grid, so the chunks read its E^{-1} rows from L2 after the first.
-constexpr int kCoarseRpt = 2;  // rows of y_c per thread
-constexpr int kCoarseThreads = kCoarseRows / kCoarseRpt;
+// Coarse level of one subdomain in SIMT arithmetic (grid: x = row block x column chunk,
+// y = subdomain).  Block (rb, chunk) forms r_c = Z^T r for the chunk's kCoarseCols
+// columns from the tile partials, then rows [rb R, (rb + 1) R) of y_c = E^{-1} r_c
+// (stored for the p update), R = kCoarseThreads kCoarseRpt with kCoarseRpt rows per
+// thread (1 up to 256 aggregates, else 2), and their part of r_c.y_c.  The last block
+// of the subdomain (atomic ticket) adds the parts in row-block order, r.M^{-1}r = fine
+// part + r_c.y_c, and in mode STEP takes the convergence test on the recursive residual
+// and beta = (r.z)_new / (r.z)_old; INIT / REPLACE: rz only (beta and gam come from the
+// init / replacement kernel).  Without a coarse level y_c = 0.  The blocks of one row
+// block are adjacent in the grid, so the chunks read its E^{-1} rows from L2 after the
+// first.
+constexpr int kCoarseThreads = 256;
 constexpr size_t kCoarseRedBytes = sizeof(double) * (kCoarseThreads / 32) * kCoarseCols;
-template <typename T>
+template <typename T, int kCoarseRpt>  // rows of y_c per thread
 __global__ void __launch_bounds__(kCoarseThreads)
     k_cg_coarse(DTiles tl, int kp, double tol2, int mode, CgState s, Coarse<T> co) {
+  constexpr int kCoarseRows = kCoarseThreads * kCoarseRpt;
   constexpr int CW = kCoarseCols;
   constexpr int PN = Pack<T>::N;
   Geo g = geo();
@@ -1371,8 +1373,11 @@ void launch_coarse_then_p(const DTiles& tiles, int n_sd, const T* r, T* p, const
                           cudaStream_t st, const cudaEvent_t* ev_mid) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute((const void*)k_cg_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(align16(sizeof(T) * kMaxAgg * kCoarseCols) + kCoarseRedBytes));
+    const int mx = (int)(align16(sizeof(T) * kMaxAgg * kCoarseCols) + kCoarseRedBytes);
+    cudaFuncSetAttribute((const void*)k_cg_coarse<T, 1>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute((const void*)k_cg_coarse<T, 2>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     attr = true;
   }
   const int n_max = co.aloc ? co.n_max : 0;
@@ -1404,10 +1409,14 @@ void launch_coarse_then_p(const DTiles& tiles, int n_sd, const T* r, T* p, const
     }
   }
   const size_t sm = align16(sizeof(T) * ((n_max + 7) & ~7) * kCoarseCols) + kCoarseRedBytes;
-  const int nrb = std::max(1, (n_max + kCoarseRows - 1) / kCoarseRows);
+  const int rows = n_max > kCoarseThreads ? 2 * kCoarseThreads : kCoarseThreads;
+  const int nrb = std::max(1, (n_max + rows - 1) / rows);
   const int nchunk = (kp + kCoarseCols - 1) / kCoarseCols;
   dim3 grid(nrb * nchunk, n_sd);
-  k_cg_coarse<T><<<grid, kCoarseThreads, sm, st>>>(tiles, kp, tol2, mode, s, co);
+  if (rows > kCoarseThreads)
+    k_cg_coarse<T, 2><<<grid, kCoarseThreads, sm, st>>>(tiles, kp, tol2, mode, s, co);
+  else
+    k_cg_coarse<T, 1><<<grid, kCoarseThreads, sm, st>>>(tiles, kp, tol2, mode, s, co);
   if (ev_mid) cudaEventRecord(*ev_mid, st);
   k_cg_update_p<T><<<tiles.n, bl, smem_bytes<T>(bl.x, bl.y, kp, 0), st>>>(tiles, r, p, dinv,
                                                                          kp, s, co);
