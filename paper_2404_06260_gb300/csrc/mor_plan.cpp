@@ -565,6 +565,23 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
                (ss.B.empty() ? " has an empty boundary set B (its extension covers the "
                                "domain: use more subdomains or fewer hops)"
                              : " has an empty interior set I");
+    // clear the element flags for the next subdomain on this thread
+    for (int32_t e : ss.plus_tets) S.tplus[e] = 0;
+  });
+  // the rest per subdomain, largest T_i^+ first (the tasks differ in size by 2-3x on
+  // box partitions; dynamic scheduling then ends the pass evenly across the threads)
+  std::vector<int> order(nw);
+  for (int li = 0; li < nw; ++li) order[li] = li;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return w.sets[a].plus_tets.size() > w.sets[b].plus_tets.size();
+  });
+  parallel_for(nw, nthr, [&](int oi, int t) {
+    Scratch& S = scratch[t];
+    const int li = order[oi];
+    const int i = s0 + li;
+    const int32_t st = i + 1;
+    SubSets& ss = w.sets[li];
+    SubOut& so = outs[li];
     // omega_i = elements touching P_i, ascending
     for (int32_t v : g.Pown[i])
       for (int64_t q = n2t_ptr[v]; q < n2t_ptr[v + 1]; ++q) {
@@ -614,7 +631,6 @@ int build_wave_plan(int64_t n_nodes, int64_t n_tets, const int32_t* tets,
                  S.rows);
     }
     // clear the element flags for the next subdomain on this thread
-    for (int32_t e : ss.plus_tets) S.tplus[e] = 0;
     for (int32_t e : ss.omega_tets) S.tomega[e] = 0;
   });
   for (auto& o : outs)
