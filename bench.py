@@ -154,16 +154,17 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def ncu_traffic(kernel_key):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if its source
-    fingerprint still matches the current sources (else None)."""
+def ncu_traffic(kernel_key, workload):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it was taken
+    on this workload and its source fingerprint still matches the current sources (else
+    None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         data = json.load(fh)
     entry = data.get(kernel_key)
-    if not entry:
+    if not entry or not entry.get("workload", "").startswith(workload + " "):
         return None
     from paper_2404_06260_gb300 import _build
     if entry.get("source_fingerprint") != _build.source_fingerprint():
@@ -373,7 +374,7 @@ def ours(args):
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "peak_source": src, "launches": int(fd["launches"]),
             "algorithmic_bytes_per_launch": per_launch_bytes,
-            "traffic": ncu_traffic(mor.KERNEL_FAMILIES[dom]),
+            "traffic": ncu_traffic(mor.KERNEL_FAMILIES[dom], args.workload),
             "time_share_of_step": fd["ms"] / t_ms,
             "families": {mor.KERNEL_FAMILIES[f]: {"ms": fams[f]["ms"],
                                                  "launches": int(fams[f]["launches"]),
