@@ -99,3 +99,23 @@ def test_tensor_core_coarse_product_matches_simt(mor):
     assert np.all(np.abs(it1 - it0) <= 8), (it0, it1)
     assert np.max(np.abs(out[1][1] - out[0][1])) <= 1e-7 * out[0][1].max()
     assert abs(out[1][2] - out[0][2]) <= 1e-8 * out[0][2]
+
+
+def test_binary64_coarse_levels_agree(mor):
+    # the binary64 path's SIMT coarse product with one row per thread (300-row
+    # aggregates, at most 256 per subdomain) and two rows per thread (35-row aggregates,
+    # about 1,000): different preconditioners, the same solutions to the CG tolerance
+    mesh, kappa, owner, p = synth.workload("cube64_p4")
+    gm = mor.Mesh(mesh.xyz, mesh.tets, kappa, mesh.dirichlet)
+    sd = mor.Subdomains(gm, owner, p["r_hops"])
+    out = {}
+    for rows in (300, 35):
+        b = mor.Bases(sd, mor.basis_opts(rank=p["rank"], oversample=p["oversample"],
+                                         seed=p["seed"], precision="fp64", cg_rtol=1e-11,
+                                         coarse_rows=rows))
+        assert b.converged
+        x, info = mor.Reduced(sd, b).solve(rtol=1e-12)
+        out[rows] = (b.stats(), b.sigma(), info["energy"])
+    assert out[35][0][:4].sum() < out[300][0][:4].sum()
+    assert np.max(np.abs(out[35][1] - out[300][1])) <= 1e-9 * out[300][1].max()
+    assert abs(out[35][2] - out[300][2]) <= 1e-9 * out[300][2]
