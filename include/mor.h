@@ -325,8 +325,11 @@ int mor_solve_reduced_noalloc(int32_t n_sub, int32_t kq, const int32_t* nbr_ptr_
                               int32_t max_iter, void* stream, double* x_dev,
                               mor_solve_info* info);
 
-/* Budget of every bounded device-side wait (grid barriers of mor_solve_reduced), in
- * seconds of the GPU's SM clock (default 1 s; a barrier normally waits microseconds).
+/* Budget of every bounded device-side wait (grid barriers of mor_solve_reduced, the
+ * mbarrier waits of the tensor-core kernels), in seconds of the GPU's SM clock
+ * (default 1 s; a wait normally lasts microseconds), between 1 ms and 3600 s
+ * (MOR_ERR_ARG otherwise): a tensor-core kernel whose wait ran out waits once more, with
+ * the same budget, for its MMAs in flight before it releases its tensor memory.
  * Process-wide, not thread-safe.  The paper has no counterpart. */
 int mor_set_wait_budget(double seconds);
 

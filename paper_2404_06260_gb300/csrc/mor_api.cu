@@ -1807,8 +1807,10 @@ int mor_solve_reduced(const mor_reduced* h, double rtol, int32_t max_iter, void*
 }
 
 int mor_set_wait_budget(double seconds) {
-  if (!(seconds >= 0.0) || seconds > 3600.0)
-    return fail(MOR_ERR_ARG, "mor_set_wait_budget: seconds must lie in [0, 3600]");
+  // at least 1 ms: after a wait runs out, the tensor-core kernels wait once more, with
+  // the same budget, for their MMAs in flight (microseconds) before releasing TMEM
+  if (!(seconds >= 1e-3) || seconds > 3600.0)
+    return fail(MOR_ERR_ARG, "mor_set_wait_budget: seconds must lie in [0.001, 3600]");
   g_wait_budget_s = seconds;
   return MOR_OK;
 }

@@ -47,4 +47,7 @@ def test_wait_on_an_unset_flag_times_out_and_the_context_survives(mor):
 def test_wait_budget_argument_checks(mor):
     with pytest.raises(mor.MorError):
         mor.set_wait_budget(-1.0)
+    with pytest.raises(mor.MorError):
+        mor.set_wait_budget(0.0)   # below the 1 ms floor the MMA drain needs
+    mor.set_wait_budget(1e-3)
     mor.set_wait_budget(1.0)
